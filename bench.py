@@ -1,0 +1,339 @@
+#!/usr/bin/env python3
+"""Benchmark of the fused FDLB time step (arXiv:1010.4124) on GB300.
+
+Workload (default): the 4096 x 4096 Kelvin-Helmholtz shear layer in FP32
+(D_v = D_rho = 16 cells, four seeded modes, dx = dy = 0.002, dt = tau = 1e-5,
+periodic in x, outflow in y), the roofline configuration of the method.  One
+"step" is one time step of the whole grid (one launch of the fused kernel).
+
+Prints ONE JSON line (rank 0):
+  value   Gcell-updates/s = nx * ny * steps / device time of the timed steps
+          (inputs resident in HBM; 2 x 1.29 GB of f >> 129 MB L2, so every
+          step streams from HBM without an explicit flush)
+  e2e     the same metric through the C ABI with host buffers: klb_init_fields
+          from pinned host fields, the steps, klb_moments back to pinned host
+          memory, all inside the timed region
+  roofline, cpu_baseline, clocks, gpu_launches.
+
+--impl reference times the FP64 CPU oracle (the baseline of this method: the
+paper publishes no timings) on a bounded sample of the same workload.
+N > 1 (torchrun): replicas only -- every rank runs its own copy of the
+workload (the step does not need a collective); value sums over ranks and the
+time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_NODE = {"fp32": 152, "fp64": 304}  # 19 reads + 19 writes per node-update
+STEP_KERNEL_SOURCES = ["paper_1010_4124_gb300/csrc/klb_step.cu", "paper_1010_4124_gb300/csrc/klb_device.cuh"]
+
+
+def kernel_sha() -> str:
+    h = hashlib.sha256()
+    for f in STEP_KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def profiled_traffic(workload: str, precision: str):
+    """Bytes per launch from the committed ncu summary, if taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", f"step_{precision}_{workload}.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    if d.get("kernel_sha") != kernel_sha():
+        return None
+    return d.get("traffic_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.tmp = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        self.tmp.flush()
+        rows = []
+        for line in open(self.tmp.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.tmp.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def workload_problem(name: str, steps: int):
+    from paper_1010_4124_gb300 import inputs
+    if name == "khi4096":
+        pb = inputs.roofline_4096(steps)
+    elif name == "khi2048":  # the same profile at 2048^2 (profiling case: 2 x 318 MB of f, > L2)
+        pb = inputs.khi(2048, 2048, steps, Dv=16.0, Drho=16.0, modes=4, phase_seed=inputs.ROOFLINE_PHASE_SEED)
+    elif name == "khi512":
+        pb = inputs.khi(512, 512, steps)
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    pb.sample_every = 0
+    return pb
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1010_4124_gb300 import inputs, klb
+
+    pb = workload_problem(args.workload, args.steps)
+    prec = args.precision
+    stream = torch.cuda.Stream()
+    fields = [np.ascontiguousarray(a) for a in inputs.fields(pb)]
+    h = klb.Klb.from_problem(pb, precision=prec, stream=stream.cuda_stream)
+    h.init_fields(*fields)
+    h.step(args.warmup)
+    h.sync()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # ---- device-resident timing: K steps bracketed by events on the launch stream
+    n0 = h.launch_count
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        h.step(args.steps)
+        e1.record(stream)
+        e1.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    launches = h.launch_count - n0
+    ms = e0.elapsed_time(e1)
+    clocks = clk.summary()
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    cells = pb.nx * pb.ny
+    value = cells * args.steps * ws / (ms * 1e-3) / 1e9
+    per_step_ms = ms / args.steps
+    achieved = BYTES_PER_NODE[prec] * cells / (per_step_ms * 1e-3) / 1e9  # GB/s
+    peak, peak_kind = measured_peaks()
+
+    # ---- end to end through the C ABI with host buffers (pinned)
+    pin = [torch.from_numpy(a).pin_memory() for a in fields]
+    outs = [torch.empty((pb.ny, pb.nx), dtype=torch.float64).pin_memory() for _ in range(4)]
+    h.sync()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h.init_fields(*[p.numpy() for p in pin])
+    h.step(args.steps)
+    h.moments(tuple(o.numpy() for o in outs))  # synchronises
+    t1 = time.perf_counter()
+    e2e_s = t1 - t0
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h.close()
+
+    line = {
+        "metric": "Gcell-updates/s (fused FDLB D2V19 WENO5 step)",
+        "value": round(value, 4),
+        "unit": "Gcell-updates/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(per_step_ms, 5),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if prec == "fp32" else "f64",
+        "data": "synthetic (seeded KHI initial fields; f = f_eq of them)",
+        "config": {"workload": f"KHI {pb.nx}x{pb.ny} {prec.upper()}, D_v=D_rho=16 cells, 4 seeded modes, "
+                               f"periodic x / outflow y, dt=tau=1e-5, dx=dy=0.002",
+                   "nx": pb.nx, "ny": pb.ny, "precision": prec, "diagnostics": "off in the timed steps",
+                   "l2": "inputs larger than L2 (2 x 1.29 GB of f per step)",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                     "traffic": profiled_traffic(args.workload, prec),
+                     "algorithmic_bytes_per_node": BYTES_PER_NODE[prec], "kernel": "fdlb::step_kernel"},
+        "e2e": {"value": round(cells * args.steps * ws / e2e_s / 1e9, 4), "unit": "Gcell-updates/s",
+                "h2d_bytes_per_step": round(4 * 8 * cells / args.steps, 1),
+                "d2h_bytes_per_step": round(4 * 8 * cells / args.steps, 1)},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.workload, samples=3)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def _band(pb, rows: int):
+    """A full-width band of `rows` rows centred on the shear layer of the workload."""
+    from paper_1010_4124_gb300 import inputs
+    band = pb.with_(ny=rows)
+    full = inputs.fields(pb)
+    j0 = pb.ny // 2 - rows // 2
+    return band, [a[j0:j0 + rows].copy() for a in full]
+
+
+def cpu_baseline(workload: str, samples: int = 3, rows: int = 256):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload: a
+    full-width band of `rows` rows around the shear layer (outflow rows), a few steps."""
+    import numpy as np
+    from oracle import core
+    pb = workload_problem(workload, 1)
+    band, fl = _band(pb, rows)
+    p = core.Params(nx=band.nx, ny=band.ny, dx=band.dx, dy=band.dy, dt=band.dt, tau=band.tau, v=band.v,
+                    bc_x=band.bc_x, bc_y=band.bc_y)
+    f = core.init_feq(p, *fl)
+    core.step(p, f)  # warm-up (page-in, thread start)
+    t0 = time.perf_counter()
+    for _ in range(samples):
+        f = core.step(p, f)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": round(band.nx * band.ny * samples / dt / 1e9, 6), "unit": "Gcell-updates/s",
+            "cores": cores, "kind": "oracle",
+            "sample": f"{samples} oracle steps (FP64, OpenMP over rows) on a {band.nx}x{band.ny} full-width band "
+                      f"of the {pb.nx}x{pb.ny} workload around the shear layer"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import build as obuild
+    obuild.build()
+    import numpy as np
+    from oracle import core
+    pb = workload_problem(args.workload, 1)
+    rows = 64
+    band, fl = _band(pb, rows)
+    p = core.Params(nx=band.nx, ny=band.ny, dx=band.dx, dy=band.dy, dt=band.dt, tau=band.tau, v=band.v,
+                    bc_x=band.bc_x, bc_y=band.bc_y)
+    f = core.init_feq(p, *fl)
+    for _ in range(args.warmup):
+        f = core.step(p, f)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f = core.step(p, f)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    value = band.nx * band.ny * args.steps / dt / 1e9
+    sample = (f"each step = one oracle step (FP64, OpenMP over rows) on a {band.nx}x{band.ny} full-width band "
+              f"of the {pb.nx}x{pb.ny} workload around the shear layer")
+    print(json.dumps({
+        "impl": "reference", "metric": "Gcell-updates/s (fused FDLB D2V19 WENO5 step)", "value": round(value, 6),
+        "unit": "Gcell-updates/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(dt / args.steps * 1e3, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"KHI {pb.nx}x{pb.ny} {args.precision.upper()}, D_v=D_rho=16 cells, 4 seeded modes, "
+                               f"periodic x / outflow y, dt=tau=1e-5, dx=dy=0.002",
+                   "nx": pb.nx, "ny": pb.ny, "precision": args.precision},
+        "cpu_baseline": {"value": round(value, 6), "unit": "Gcell-updates/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 6), "unit": "Gcell-updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="khi4096", choices=["khi4096", "khi2048", "khi512"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

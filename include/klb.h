@@ -1,0 +1,168 @@
+/*
+ * klb.h -- C ABI of the GB300 (sm_103a) finite-difference lattice Boltzmann
+ * time step of Gan, Xu, Zhang & Li, "Lattice Boltzmann study on
+ * Kelvin-Helmholtz instability: the roles of velocity and density gradients"
+ * (arXiv:1010.4124).
+ *
+ * The method (Secs. II-III of the paper): 19 discrete velocities (a rest
+ * velocity plus three rings of six directions, Eq. 5); the truncated
+ * equilibrium f^(0) from the moments rho, u, T through the closed-form global
+ * coefficients F_k(T) (Eqs. 10, 28, 44-46); the convection term v . grad f by
+ * fifth-order WENO finite differences of F = v_alpha f, upwinded by the sign of
+ * each velocity component (Eqs. 48-55 and the mirror procedure that follows
+ * them); BGK relaxation and forward-Euler time integration (Eq. 47); ghost-node
+ * boundaries: periodic, outflow by zeroth-order extrapolation (Eqs. 63-64) and
+ * fixed equilibrium (Eqs. 57-58).
+ *
+ * Conventions of every entry point:
+ *  - Return value: KLB_OK (0) or a negative KLB_E_* code; klb_last_error()
+ *    gives a one-line message for the handle's last failure.
+ *  - Host-facing arrays are always double, C order, owned by the caller.
+ *    Macroscopic fields are [ny][nx] (x fastest); a distribution array is
+ *    [19][ny][nx].  `on_device` = 1 means the pointer is a CUDA device pointer
+ *    (e.g. from torch), 0 means host memory (pinned memory gives the fastest
+ *    copies).
+ *  - The library owns all device memory of a handle (two copies of f plus
+ *    small buffers), allocated in klb_create and freed in klb_destroy.
+ *  - Work is enqueued on the handle's stream; calls that return data to the
+ *    caller synchronise that stream.  Errors raised by kernels (a bounded wait
+ *    that ran out, a non-finite state) surface at the next synchronising call.
+ *  - A handle is not thread-safe; separate handles are independent.
+ *
+ * Velocity index q: 0 is the rest velocity; q = 1 + 6(k-1) + (i-1) is ring
+ * k = 1..3 (speed v[k-1]) in direction i = 1..6 at angle 60 i degrees.
+ */
+#ifndef KLB_H
+#define KLB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KLB_OK 0
+#define KLB_E_INVAL (-1)          /* an argument is out of range */
+#define KLB_E_NOMEM (-2)          /* device or host allocation failed */
+#define KLB_E_CUDA (-3)           /* a CUDA runtime call failed */
+#define KLB_E_NONFINITE (-4)      /* a sampled state had rho or T non-finite or <= 0 */
+#define KLB_E_DEVICE_TIMEOUT (-5) /* a bounded device-side wait ran out */
+#define KLB_E_STATE (-6)          /* call out of order (e.g. step before init) */
+#define KLB_E_IO (-7)             /* file I/O failed (save / load) */
+
+typedef enum { KLB_BC_PERIODIC = 0, KLB_BC_OUTFLOW = 1, KLB_BC_FIXED_EQ = 2 } klb_bc;
+typedef enum { KLB_FP32 = 0, KLB_FP64 = 1 } klb_prec;
+
+/* Problem statement of one run (Sec. III.B, Sec. IV of the paper). */
+typedef struct {
+    int32_t nx, ny;           /* interior nodes in x (fastest) and y; >= 1 each */
+    double dx, dy;            /* node spacing, > 0 */
+    double dt;                /* time step, > 0 */
+    double tau;               /* BGK relaxation time, > 0 */
+    double v[3];              /* ring speeds v_1, v_2, v_3: distinct, > 0; the paper uses 1, 2, 3 */
+    int32_t bc_x_lo, bc_x_hi; /* klb_bc of the x = 0 and x = nx-1 sides; periodic must pair */
+    int32_t bc_y_lo, bc_y_hi; /* same for y */
+    int32_t precision;        /* klb_prec: storage and arithmetic type of f on the device */
+    int32_t sample_every;     /* diagnostics every n steps (0 = off); see klb_diagnostics */
+    int32_t diag_capacity;    /* samples kept on the device (0 = 4096); older samples are dropped */
+    double eps;               /* WENO epsilon of Eq. 52; 0 selects the paper's 1e-6 */
+    void* stream;             /* cudaStream_t to enqueue on; NULL = a stream owned by the handle */
+} klb_params;
+
+typedef struct klb klb_t;
+
+/* Fill `p` with the defaults: v = {1,2,3}, all sides periodic, FP32,
+ * sample_every 0, eps 1e-6, NULL stream.  nx, ny, dx, dy, dt, tau stay 0 and
+ * must be set by the caller. */
+void klb_params_default(klb_params* p);
+
+/* Validate `p`, allocate the device state on the current CUDA device and
+ * return a handle in *out.  Ownership: the caller destroys it with
+ * klb_destroy.  Logs (stderr) a warning when dt/tau > 2 or the convective CFL
+ * number max(v) dt / min(dx, dy) > 0.03 (forward Euler with WENO5 then grows
+ * linearly unstable modes).  Errors: KLB_E_INVAL, KLB_E_NOMEM, KLB_E_CUDA. */
+int klb_create(const klb_params* p, klb_t** out);
+
+/* Free every resource of the handle.  NULL-safe. */
+void klb_destroy(klb_t* h);
+
+/* Initial state (Sec. III.B Eq. 56, Sec. IV Eqs. 59-62): f := f^(0)(rho, u, T)
+ * at every node, ghost nodes filled, and the fixed-equilibrium ghost values of
+ * Eq. 57 taken from the edge nodes of these fields.  Fields are [ny][nx]
+ * doubles; T > 0 and rho > 0.  Resets the step counter and the diagnostics
+ * series (the state at step 0 is sampled when sample_every > 0).  Errors:
+ * KLB_E_INVAL (NULL pointer), KLB_E_CUDA. */
+int klb_init_fields(klb_t* h, const double* rho, const double* ux, const double* uy,
+                    const double* T, int on_device);
+
+/* Overwrite the interior distribution with f[19][ny][nx] (doubles, converted
+ * to the handle's precision) and refresh the periodic / outflow ghost nodes.
+ * Fixed-equilibrium ghosts keep the values set by klb_init_fields.  Requires a
+ * prior klb_init_fields (KLB_E_STATE otherwise). */
+int klb_set_f(klb_t* h, const double* f, int on_device);
+
+/* Copy the interior distribution to f[19][ny][nx] (doubles).  Synchronises. */
+int klb_get_f(klb_t* h, double* f, int on_device);
+
+/* Enqueue n time steps (Eq. 47) on the handle's stream and return without
+ * waiting.  Each step is one launch of the fused step kernel (ghost images of
+ * the new state are written by the same launch).  n >= 0.  Errors:
+ * KLB_E_STATE (no klb_init_fields yet), KLB_E_INVAL, KLB_E_CUDA. */
+int klb_step(klb_t* h, int64_t n);
+
+/* Wait for the handle's stream; report device-side errors recorded since the
+ * last synchronising call (KLB_E_DEVICE_TIMEOUT, KLB_E_NONFINITE). */
+int klb_sync(klb_t* h);
+
+/* Macroscopic fields (Eq. 10) of the current state into caller-owned [ny][nx]
+ * double arrays: rho, u_x, u_y and T (P = rho T).  Any pointer may be NULL to
+ * skip that field.  Synchronises. */
+int klb_moments(klb_t* h, double* rho, double* ux, double* uy, double* T, int on_device);
+
+/* Diagnostics series (Sec. IV): one record of 7 doubles per sample, taken on
+ * the states after 0, s, 2s, ... steps (s = sample_every):
+ *   [0] sum rho, [1] sum rho u_x, [2] sum rho u_y, [3] sum rho (T + |u|^2/2),
+ *   [4] max |u_y|, [5] max rho u_y^2 / 2, [6] sum rho u_y^2 / 2,
+ * sums over interior nodes (unweighted), accumulated in FP64 in a fixed order
+ * (deterministic).  Copies min(cap, available) records, oldest first, into
+ * out[cap][7] (host) and the number copied into *count.  Synchronises; returns
+ * KLB_E_NONFINITE if any sampled state had rho or T non-finite or <= 0. */
+int klb_diagnostics(klb_t* h, double* out, int64_t cap, int64_t* count);
+
+/* Number of steps taken since klb_init_fields. */
+int64_t klb_step_count(const klb_t* h);
+
+/* Checkpoint / resume: write (or read) the parameters, the step counter, the
+ * diagnostics series and both the interior and ghost nodes of f in the
+ * handle's precision, so that a resumed run continues bitwise identically.
+ * klb_load requires a handle created with the same nx, ny and precision.
+ * Errors: KLB_E_IO, KLB_E_INVAL (mismatch), KLB_E_CUDA. */
+int klb_save(klb_t* h, const char* path);
+int klb_load(klb_t* h, const char* path);
+
+/* Message of the handle's last error ("" if none); with h == NULL, the last
+ * error of a failed klb_create on this thread. */
+const char* klb_last_error(const klb_t* h);
+
+/* Device layout of f, for profilers and tests: base pointer of the current
+ * state, row pitch and plane stride in elements, and the offsets (gx, gy) of
+ * interior node (0,0) inside a plane.  Element (q, j, i) of the interior is
+ * at base[q*plane + (j+gy)*pitch + (i+gx)]. */
+int klb_layout(const klb_t* h, const void** base, int64_t* pitch, int64_t* plane,
+               int32_t* gx, int32_t* gy);
+
+/* Kernel launches enqueued by this handle since klb_create (every kernel the
+ * library launched on its stream). */
+int64_t klb_launch_count(const klb_t* h);
+
+/* Fault injection for tests: the number of polls each step-kernel CTA grants
+ * its bounded wait on the shared-memory tile load (default 2^22).  With a
+ * small value the wait runs out, the kernel records KLB_E_DEVICE_TIMEOUT
+ * (reported by the next synchronising call), lets the copy in flight land and
+ * exits without computing; the context stays usable.  polls >= 1. */
+int klb_debug_set_spin_limit(klb_t* h, int64_t polls);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KLB_H */

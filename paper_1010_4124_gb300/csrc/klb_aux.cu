@@ -1,0 +1,246 @@
+// klb_aux.cu -- small kernels around the step: initial equilibrium state,
+// fixed-equilibrium ghosts, distribution import / export, macroscopic fields,
+// and the diagnostics reduction.  All of them are elementwise or single-pass
+// reductions; none is on the per-step hot path except the diagnostics
+// finalisation (one tiny launch per sample).
+#include "klb_launch.h"
+
+namespace fdlb {
+
+// f := f^(0)(rho, u, T) at every interior node (Eq. 28), written to both
+// ping-pong buffers with ghost images.
+template <typename T>
+__global__ void init_feq_kernel(const StepConst<T> c, const Geom g, const double* __restrict__ rho,
+                                const double* __restrict__ ux, const double* __restrict__ uy,
+                                const double* __restrict__ Tm, T* __restrict__ a, T* __restrict__ b) {
+    const long long n = (long long)g.nx * g.ny;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const int ix = (int)(k % g.nx), iy = (int)(k / g.nx);
+        NodeEq<T> s;
+        s.rho = T(rho[k]);
+        s.ux = T(ux[k]);
+        s.uy = T(uy[k]);
+        s.Tm = T(Tm[k]);
+        T iT = T(1) / s.Tm;
+        T u2 = s.ux * s.ux + s.uy * s.uy;
+        s.A = T(1) - T(0.5) * u2 * iT;
+        s.a = s.ux * iT;
+        s.b = s.uy * iT;
+        T F[4];
+        global_coeffs(c, s.Tm, F);
+        for (int j = 0; j < 4; ++j) s.rF[j] = s.rho * F[j];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            T v = feq_q(c, s, q);
+            store_with_images(a, g, q, ix, iy, v);
+            store_with_images(b, g, q, ix, iy, v);
+        }
+    }
+}
+
+// Fixed-equilibrium ghosts (Eq. 57): the three ghost nodes beyond an edge node
+// hold f^(0) of that node's initial state, for every side with FIXED_EQ.
+template <typename T>
+__global__ void fixed_ghosts_kernel(const StepConst<T> c, const Geom g, const double* __restrict__ rho,
+                                    const double* __restrict__ ux, const double* __restrict__ uy,
+                                    const double* __restrict__ Tm, T* __restrict__ a, T* __restrict__ b) {
+    // items: [0, ny) x-lo rows, [ny, 2ny) x-hi rows, then nx columns y-lo, nx y-hi
+    const int total = 2 * g.ny + 2 * g.nx;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        int side, ix, iy;
+        if (t < 2 * g.ny) {
+            side = t < g.ny ? 0 : 1;
+            iy = t % g.ny;
+            ix = side == 0 ? 0 : g.nx - 1;
+            if ((side == 0 ? g.bcx_lo : g.bcx_hi) != 2) continue;
+        } else {
+            int u = t - 2 * g.ny;
+            side = u < g.nx ? 2 : 3;
+            ix = u % g.nx;
+            iy = side == 2 ? 0 : g.ny - 1;
+            if ((side == 2 ? g.bcy_lo : g.bcy_hi) != 2) continue;
+        }
+        const long long k = (long long)iy * g.nx + ix;
+        NodeEq<T> s;
+        s.rho = T(rho[k]);
+        s.ux = T(ux[k]);
+        s.uy = T(uy[k]);
+        s.Tm = T(Tm[k]);
+        T iT = T(1) / s.Tm;
+        T u2 = s.ux * s.ux + s.uy * s.uy;
+        s.A = T(1) - T(0.5) * u2 * iT;
+        s.a = s.ux * iT;
+        s.b = s.uy * iT;
+        T F[4];
+        global_coeffs(c, s.Tm, F);
+        for (int j = 0; j < 4; ++j) s.rF[j] = s.rho * F[j];
+        for (int q = 0; q < NQ; ++q) {
+            T v = feq_q(c, s, q);
+            for (int d = 1; d <= 3; ++d) {
+                long long off;
+                if (side == 0) off = (long long)(iy + GY) * g.px + (GX - d);
+                else if (side == 1) off = (long long)(iy + GY) * g.px + (g.nx - 1 + GX + d);
+                else if (side == 2) off = (long long)(GY - d) * g.px + (ix + GX);
+                else off = (long long)(g.ny - 1 + GY + d) * g.px + (ix + GX);
+                a[q * g.plane + off] = v;
+                b[q * g.plane + off] = v;
+            }
+        }
+    }
+}
+
+template <typename T>
+__global__ void set_f_kernel(const Geom g, const double* __restrict__ src, T* __restrict__ dst) {
+    const long long n = (long long)g.nx * g.ny;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < NQ * n; k += (long long)gridDim.x * blockDim.x) {
+        const int q = (int)(k / n);
+        const long long r = k % n;
+        store_with_images(dst, g, q, (int)(r % g.nx), (int)(r / g.nx), T(src[k]));
+    }
+}
+
+template <typename T>
+__global__ void get_f_kernel(const Geom g, const T* __restrict__ src, double* __restrict__ dst) {
+    const long long n = (long long)g.nx * g.ny;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < NQ * n; k += (long long)gridDim.x * blockDim.x) {
+        const int q = (int)(k / n);
+        const long long r = k % n;
+        const int ix = (int)(r % g.nx), iy = (int)(r / g.nx);
+        dst[k] = double(src[q * g.plane + (long long)(iy + GY) * g.px + (ix + GX)]);
+    }
+}
+
+template <typename T>
+__global__ void fields_kernel(const StepConst<T> c, const Geom g, const T* __restrict__ f,
+                              double* __restrict__ rho, double* __restrict__ ux, double* __restrict__ uy,
+                              double* __restrict__ Tm) {
+    const long long n = (long long)g.nx * g.ny;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const int ix = (int)(k % g.nx), iy = (int)(k / g.nx);
+        T fl[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) fl[q] = f[q * g.plane + (long long)(iy + GY) * g.px + (ix + GX)];
+        NodeEq<T> s = node_state(c, fl);
+        if (rho) rho[k] = s.rho;
+        if (ux) ux[k] = s.ux;
+        if (uy) uy[k] = s.uy;
+        if (Tm) Tm[k] = s.Tm;
+    }
+}
+
+// Diagnostics partials of a state over the same TX x TY tiles, in the same
+// reduction order, as the fused path inside the step kernel.
+template <typename T, int TX, int TY>
+__global__ void __launch_bounds__(TX* TY) diag_partials_kernel(const StepConst<T> c, const Geom g,
+                                                               const T* __restrict__ f,
+                                                               double* __restrict__ partials) {
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    const int ix = blockIdx.x * TX + tx, iy = blockIdx.y * TY + ty;
+    const bool active = ix < g.nx && iy < g.ny;
+    T fl[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) fl[q] = active ? f[q * g.plane + (long long)(iy + GY) * g.px + (ix + GX)] : T(1);
+    NodeEq<T> s = node_state(c, fl);
+    double v[8];
+    node_diag(s, active, v);
+    diag_block_reduce<TX * TY>(v, partials + 8ll * (blockIdx.y * gridDim.x + blockIdx.x));
+}
+
+// One block folds all partial records, in record order per thread and a fixed
+// tree across threads.
+__global__ void diag_finalize_kernel(const double* __restrict__ partials, int nparts, double* __restrict__ out,
+                                     int* __restrict__ err) {
+    __shared__ double red[256][8];
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            double x = partials[8ll * i + k];
+            acc[k] = (k == 4 || k == 5 || k == 7) ? fmax(acc[k], x) : acc[k] + x;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) red[threadIdx.x][k] = acc[k];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                double x = red[threadIdx.x + w][k];
+                red[threadIdx.x][k] = (k == 4 || k == 5 || k == 7) ? fmax(red[threadIdx.x][k], x) : red[threadIdx.x][k] + x;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 7; ++k) out[k] = red[0][k];
+        if (red[0][7] != 0.0) atomicOr(err, ERR_NONFINITE);
+    }
+}
+
+static int grid_for(long long n, int threads) {
+    long long b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > 152 * 64) b = 152 * 64;
+    return (int)b;
+}
+
+template <typename T>
+cudaError_t launch_init_feq(const StepConst<T>& c, const Geom& g, const double* rho, const double* ux,
+                            const double* uy, const double* Tm, T* a, T* b, cudaStream_t s) {
+    init_feq_kernel<T><<<grid_for((long long)g.nx * g.ny, 256), 256, 0, s>>>(c, g, rho, ux, uy, Tm, a, b);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_fixed_ghosts(const StepConst<T>& c, const Geom& g, const double* rho, const double* ux,
+                                const double* uy, const double* Tm, T* a, T* b, cudaStream_t s) {
+    fixed_ghosts_kernel<T><<<grid_for(2ll * (g.nx + g.ny), 128), 128, 0, s>>>(c, g, rho, ux, uy, Tm, a, b);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_set_f(const Geom& g, const double* src, T* dst, cudaStream_t s) {
+    set_f_kernel<T><<<grid_for(19ll * g.nx * g.ny, 256), 256, 0, s>>>(g, src, dst);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_get_f(const Geom& g, const T* src, double* dst, cudaStream_t s) {
+    get_f_kernel<T><<<grid_for(19ll * g.nx * g.ny, 256), 256, 0, s>>>(g, src, dst);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_fields(const StepConst<T>& c, const Geom& g, const T* f, double* rho, double* ux, double* uy,
+                          double* Tm, cudaStream_t s) {
+    fields_kernel<T><<<grid_for((long long)g.nx * g.ny, 256), 256, 0, s>>>(c, g, f, rho, ux, uy, Tm);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_diag_partials(const StepConst<T>& c, const Geom& g, const T* f, double* partials,
+                                 cudaStream_t s) {
+    int TX, TY;
+    step_tile_shape(sizeof(T) == 8 ? 1 : 0, &TX, &TY);
+    dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY);
+    if (sizeof(T) == 8)
+        diag_partials_kernel<T, 32, 8><<<grid, 256, 0, s>>>(c, g, f, partials);
+    else
+        diag_partials_kernel<T, 32, 16><<<grid, 512, 0, s>>>(c, g, f, partials);
+    return cudaGetLastError();
+}
+cudaError_t launch_diag_finalize(const double* partials, int nparts, double* out, int* err, cudaStream_t s) {
+    diag_finalize_kernel<<<1, 256, 0, s>>>(partials, nparts, out, err);
+    return cudaGetLastError();
+}
+
+#define KLB_INST(T)                                                                                              \
+    template cudaError_t launch_init_feq<T>(const StepConst<T>&, const Geom&, const double*, const double*,     \
+                                            const double*, const double*, T*, T*, cudaStream_t);              \
+    template cudaError_t launch_fixed_ghosts<T>(const StepConst<T>&, const Geom&, const double*, const double*, \
+                                                const double*, const double*, T*, T*, cudaStream_t);          \
+    template cudaError_t launch_set_f<T>(const Geom&, const double*, T*, cudaStream_t);                         \
+    template cudaError_t launch_get_f<T>(const Geom&, const T*, double*, cudaStream_t);                         \
+    template cudaError_t launch_fields<T>(const StepConst<T>&, const Geom&, const T*, double*, double*, double*, \
+                                          double*, cudaStream_t);                                              \
+    template cudaError_t launch_diag_partials<T>(const StepConst<T>&, const Geom&, const T*, double*, cudaStream_t);
+KLB_INST(float)
+KLB_INST(double)
+
+}  // namespace fdlb

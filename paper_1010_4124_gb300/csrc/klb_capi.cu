@@ -1,0 +1,561 @@
+// klb_capi.cu -- implementation of the C ABI declared in include/klb.h.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+
+#include "../../include/klb.h"
+#include "klb_launch.h"
+
+using namespace fdlb;
+
+struct klb {
+    klb_params p{};
+    Geom g{};
+    size_t esize = 0;             // bytes per element of f
+    void* buf[2] = {nullptr, nullptr};
+    int cur = 0;                  // buffer holding the current state
+    CUtensorMap map[2];
+    StepConst<float> cf{};
+    StepConst<double> cd{};
+    double* fields_dev = nullptr; // 4 * nx * ny doubles of staging for host fields
+    double* fdense_dev = nullptr; // 19 * nx * ny doubles of staging for host f (lazy)
+    double* diag_ring = nullptr;  // [cap][7]
+    double* diag_partials = nullptr;
+    int nparts = 0;
+    int cap = 0;
+    int* err_dev = nullptr;
+    int64_t steps = 0;
+    int64_t nsamples = 0;
+    bool pending_sample = false;
+    bool initialized = false;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int64_t launches = 0;
+    long long spin_limit = kDefaultSpin;
+    std::string err;
+};
+
+static thread_local std::string g_create_error;
+
+static int fail(klb_t* h, int code, const std::string& msg) {
+    if (h) h->err = msg;
+    else g_create_error = msg;
+    return code;
+}
+static int cuda_fail(klb_t* h, cudaError_t e, const char* where) {
+    return fail(h, KLB_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+#define CK(h, call)                                            \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// constants of the step from the problem statement
+// ---------------------------------------------------------------------------
+template <typename T>
+static void fill_const(const klb_params& p, StepConst<T>& c) {
+    const double h = 0.5 * std::sqrt(3.0);
+    const double cs[6] = {0.5, -0.5, -1.0, -0.5, 0.5, 1.0};  // cos(60 i deg), i = 1..6
+    const double sn[6] = {h, h, 0.0, -h, -h, 0.0};            // sin(60 i deg)
+    const double eps = p.eps > 0 ? p.eps : 1e-6;
+    for (int q = 0; q < NQ; ++q) {
+        double vx = 0, vy = 0;
+        if (q > 0) {
+            const int k = (q - 1) / 6, i = (q - 1) % 6;
+            vx = p.v[k] * cs[i];
+            vy = p.v[k] * sn[i];
+        }
+        c.vx[q] = T(vx);
+        c.vy[q] = T(vy);
+        c.v2[q] = T(vx * vx + vy * vy);
+        c.cx[q] = T(p.dt * vx / p.dx);
+        c.cy[q] = T(p.dt * vy / p.dy);
+        c.ex[q] = vx != 0 ? T(eps / (vx * vx)) : T(0);
+        c.ey[q] = vy != 0 ? T(eps / (vy * vy)) : T(0);
+    }
+    // F_k(T) = T [a_{k+1} a_{k+2} - 4 (a_{k+1} + a_{k+2}) T + 24 T^2] / [3 a_k (a_k - a_{k+1})(a_k - a_{k+2})]
+    for (int k = 0; k < 3; ++k) {
+        const double ak = p.v[k] * p.v[k];
+        const double a1 = p.v[(k + 1) % 3] * p.v[(k + 1) % 3];
+        const double a2 = p.v[(k + 2) % 3] * p.v[(k + 2) % 3];
+        const double den = 3.0 * ak * (ak - a1) * (ak - a2);
+        c.fk[k][0] = T(a1 * a2 / den);
+        c.fk[k][1] = T(-4.0 * (a1 + a2) / den);
+        c.fk[k][2] = T(24.0 / den);
+    }
+    c.relax = T(p.dt / p.tau);
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(ptr);
+    }
+    return fn;
+}
+
+// 3-D map over (x: pitch, y: ny + 6 rows, z: 19 planes) with the step's box.
+static int make_map(klb_t* h, void* base, CUtensorMap* map) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return fail(h, KLB_E_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    int TX, TY;
+    step_tile_shape(h->p.precision, &TX, &TY);
+    const Geom& g = h->g;
+    cuuint64_t dims[3] = {(cuuint64_t)g.px, (cuuint64_t)(g.ny + 2 * GY), (cuuint64_t)NQ};
+    cuuint64_t strides[2] = {(cuuint64_t)g.px * h->esize, (cuuint64_t)g.plane * h->esize};
+    cuuint32_t box[3] = {(cuuint32_t)(TX + 8), (cuuint32_t)(TY + 6), (cuuint32_t)NQ};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(map, h->p.precision == KLB_FP64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                    3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(h, KLB_E_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+    return KLB_OK;
+}
+
+extern "C" {
+
+void klb_params_default(klb_params* p) {
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->v[0] = 1.0;
+    p->v[1] = 2.0;
+    p->v[2] = 3.0;
+    p->bc_x_lo = p->bc_x_hi = p->bc_y_lo = p->bc_y_hi = KLB_BC_PERIODIC;
+    p->precision = KLB_FP32;
+    p->eps = 1e-6;
+}
+
+int klb_create(const klb_params* pin, klb_t** out) {
+    if (!pin || !out) return fail(nullptr, KLB_E_INVAL, "NULL argument");
+    *out = nullptr;
+    const klb_params& p = *pin;
+    if (p.nx < 1 || p.ny < 1) return fail(nullptr, KLB_E_INVAL, "nx and ny must be >= 1");
+    if ((long long)p.nx + 16 > (1ll << 31) / 2) return fail(nullptr, KLB_E_INVAL, "nx too large");
+    if (!(p.dx > 0) || !(p.dy > 0) || !(p.dt > 0) || !(p.tau > 0))
+        return fail(nullptr, KLB_E_INVAL, "dx, dy, dt and tau must be > 0");
+    for (int k = 0; k < 3; ++k)
+        if (!(p.v[k] > 0)) return fail(nullptr, KLB_E_INVAL, "ring speeds must be > 0");
+    if (p.v[0] == p.v[1] || p.v[1] == p.v[2] || p.v[0] == p.v[2])
+        return fail(nullptr, KLB_E_INVAL, "ring speeds must be distinct");
+    const int bcs[4] = {p.bc_x_lo, p.bc_x_hi, p.bc_y_lo, p.bc_y_hi};
+    for (int b : bcs)
+        if (b < 0 || b > 2) return fail(nullptr, KLB_E_INVAL, "unknown boundary kind");
+    if ((p.bc_x_lo == KLB_BC_PERIODIC) != (p.bc_x_hi == KLB_BC_PERIODIC) ||
+        (p.bc_y_lo == KLB_BC_PERIODIC) != (p.bc_y_hi == KLB_BC_PERIODIC))
+        return fail(nullptr, KLB_E_INVAL, "a periodic side must pair with a periodic side");
+    if (p.precision != KLB_FP32 && p.precision != KLB_FP64) return fail(nullptr, KLB_E_INVAL, "unknown precision");
+    if (p.sample_every < 0 || p.diag_capacity < 0) return fail(nullptr, KLB_E_INVAL, "negative diagnostics setting");
+    if (p.eps < 0) return fail(nullptr, KLB_E_INVAL, "eps must be >= 0");
+
+    const double vmax = std::max(p.v[0], std::max(p.v[1], p.v[2]));
+    const double cfl = vmax * p.dt / std::min(p.dx, p.dy);
+    if (p.dt / p.tau > 2.0)
+        fprintf(stderr, "klb: warning: dt/tau = %g > 2 (the BGK factor 1 - dt/tau exceeds -1)\n", p.dt / p.tau);
+    if (cfl > 0.03)
+        fprintf(stderr, "klb: warning: CFL max(v) dt/min(dx,dy) = %g > 0.03; forward Euler + WENO5 may grow\n", cfl);
+
+    klb_t* h = new klb();
+    h->p = p;
+    if (h->p.eps == 0) h->p.eps = 1e-6;
+    h->esize = p.precision == KLB_FP64 ? 8 : 4;
+    Geom& g = h->g;
+    g.nx = p.nx;
+    g.ny = p.ny;
+    g.px = ((p.nx + GX + 3) + 31) / 32 * 32;
+    g.plane = (long long)g.px * (p.ny + 2 * GY);
+    g.bcx_lo = p.bc_x_lo;
+    g.bcx_hi = p.bc_x_hi;
+    g.bcy_lo = p.bc_y_lo;
+    g.bcy_hi = p.bc_y_hi;
+    fill_const(h->p, h->cf);
+    fill_const(h->p, h->cd);
+    int TX, TY;
+    step_tile_shape(p.precision, &TX, &TY);
+    h->nparts = ((p.nx + TX - 1) / TX) * ((p.ny + TY - 1) / TY);
+    h->cap = p.diag_capacity > 0 ? p.diag_capacity : 4096;
+
+    auto cleanup = [&](int code) {
+        klb_destroy(h);
+        return code;
+    };
+    const size_t fbytes = (size_t)NQ * g.plane * h->esize;
+    for (int i = 0; i < 2; ++i) {
+        if (cudaMalloc(&h->buf[i], fbytes) != cudaSuccess) {
+            cudaGetLastError();
+            fail(nullptr, KLB_E_NOMEM, "cudaMalloc of the distribution buffers failed");
+            return cleanup(KLB_E_NOMEM);
+        }
+        if (cudaMemset(h->buf[i], 0, fbytes) != cudaSuccess) {
+            fail(nullptr, KLB_E_CUDA, "cudaMemset failed");
+            return cleanup(KLB_E_CUDA);
+        }
+    }
+    if (cudaMalloc(&h->fields_dev, sizeof(double) * 4 * (size_t)p.nx * p.ny) != cudaSuccess ||
+        cudaMalloc(&h->diag_ring, sizeof(double) * 7 * (size_t)h->cap) != cudaSuccess ||
+        cudaMalloc(&h->diag_partials, sizeof(double) * 8 * (size_t)h->nparts) != cudaSuccess ||
+        cudaMalloc(&h->err_dev, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        fail(nullptr, KLB_E_NOMEM, "cudaMalloc of the staging buffers failed");
+        return cleanup(KLB_E_NOMEM);
+    }
+    cudaMemset(h->err_dev, 0, sizeof(int));
+    if (p.stream) {
+        h->stream = (cudaStream_t)p.stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            fail(nullptr, KLB_E_CUDA, "cudaStreamCreate failed");
+            return cleanup(KLB_E_CUDA);
+        }
+        h->own_stream = true;
+    }
+    for (int i = 0; i < 2; ++i) {
+        int r = make_map(h, h->buf[i], &h->map[i]);
+        if (r != KLB_OK) {
+            g_create_error = h->err;
+            return cleanup(r);
+        }
+    }
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        fail(nullptr, KLB_E_CUDA, "device synchronisation after allocation failed");
+        return cleanup(KLB_E_CUDA);
+    }
+    *out = h;
+    return KLB_OK;
+}
+
+void klb_destroy(klb_t* h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    for (int i = 0; i < 2; ++i)
+        if (h->buf[i]) cudaFree(h->buf[i]);
+    if (h->fields_dev) cudaFree(h->fields_dev);
+    if (h->fdense_dev) cudaFree(h->fdense_dev);
+    if (h->diag_ring) cudaFree(h->diag_ring);
+    if (h->diag_partials) cudaFree(h->diag_partials);
+    if (h->err_dev) cudaFree(h->err_dev);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+static int stage_fields(klb_t* h, const double* rho, const double* ux, const double* uy, const double* T,
+                        int on_device, const double** d) {
+    const size_t n = (size_t)h->g.nx * h->g.ny;
+    const double* src[4] = {rho, ux, uy, T};
+    for (int i = 0; i < 4; ++i) {
+        if (!src[i]) return fail(h, KLB_E_INVAL, "NULL field pointer");
+        if (on_device) {
+            d[i] = src[i];
+        } else {
+            CK(h, cudaMemcpyAsync(h->fields_dev + i * n, src[i], n * sizeof(double), cudaMemcpyHostToDevice,
+                                  h->stream));
+            d[i] = h->fields_dev + i * n;
+        }
+    }
+    return KLB_OK;
+}
+
+int klb_init_fields(klb_t* h, const double* rho, const double* ux, const double* uy, const double* T,
+                    int on_device) {
+    if (!h) return KLB_E_INVAL;
+    const double* d[4];
+    int r = stage_fields(h, rho, ux, uy, T, on_device, d);
+    if (r != KLB_OK) return r;
+    cudaError_t e;
+    if (h->p.precision == KLB_FP64) {
+        e = launch_init_feq<double>(h->cd, h->g, d[0], d[1], d[2], d[3], (double*)h->buf[0], (double*)h->buf[1],
+                                    h->stream);
+        if (e == cudaSuccess)
+            e = launch_fixed_ghosts<double>(h->cd, h->g, d[0], d[1], d[2], d[3], (double*)h->buf[0],
+                                            (double*)h->buf[1], h->stream);
+    } else {
+        e = launch_init_feq<float>(h->cf, h->g, d[0], d[1], d[2], d[3], (float*)h->buf[0], (float*)h->buf[1],
+                                   h->stream);
+        if (e == cudaSuccess)
+            e = launch_fixed_ghosts<float>(h->cf, h->g, d[0], d[1], d[2], d[3], (float*)h->buf[0],
+                                           (float*)h->buf[1], h->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "init kernels");
+    h->launches += 2;
+    h->cur = 0;
+    h->steps = 0;
+    h->nsamples = 0;
+    h->pending_sample = h->p.sample_every > 0;
+    h->initialized = true;
+    return KLB_OK;
+}
+
+static int ensure_dense(klb_t* h) {
+    if (!h->fdense_dev) {
+        if (cudaMalloc(&h->fdense_dev, sizeof(double) * NQ * (size_t)h->g.nx * h->g.ny) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, KLB_E_NOMEM, "cudaMalloc of the distribution staging buffer failed");
+        }
+    }
+    return KLB_OK;
+}
+
+int klb_set_f(klb_t* h, const double* f, int on_device) {
+    if (!h || !f) return h ? fail(h, KLB_E_INVAL, "NULL f") : KLB_E_INVAL;
+    if (!h->initialized) return fail(h, KLB_E_STATE, "klb_set_f before klb_init_fields");
+    const double* src = f;
+    if (!on_device) {
+        int r = ensure_dense(h);
+        if (r != KLB_OK) return r;
+        CK(h, cudaMemcpyAsync(h->fdense_dev, f, sizeof(double) * NQ * (size_t)h->g.nx * h->g.ny,
+                              cudaMemcpyHostToDevice, h->stream));
+        src = h->fdense_dev;
+    }
+    cudaError_t e = h->p.precision == KLB_FP64
+                        ? launch_set_f<double>(h->g, src, (double*)h->buf[h->cur], h->stream)
+                        : launch_set_f<float>(h->g, src, (float*)h->buf[h->cur], h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "set_f kernel");
+    h->launches += 1;
+    return KLB_OK;
+}
+
+static int check_err(klb_t* h) {
+    int v = 0;
+    CK(h, cudaMemcpyAsync(&v, h->err_dev, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (v) {
+        CK(h, cudaMemsetAsync(h->err_dev, 0, sizeof(int), h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        if (v & ERR_TIMEOUT) return fail(h, KLB_E_DEVICE_TIMEOUT, "a bounded device-side wait ran out");
+        if (v & ERR_NONFINITE) return fail(h, KLB_E_NONFINITE, "a sampled state had rho or T non-finite or <= 0");
+    }
+    return KLB_OK;
+}
+
+int klb_sync(klb_t* h) {
+    if (!h) return KLB_E_INVAL;
+    CK(h, cudaStreamSynchronize(h->stream));
+    return check_err(h);
+}
+
+int klb_get_f(klb_t* h, double* f, int on_device) {
+    if (!h || !f) return h ? fail(h, KLB_E_INVAL, "NULL f") : KLB_E_INVAL;
+    if (!h->initialized) return fail(h, KLB_E_STATE, "klb_get_f before klb_init_fields");
+    double* dst = f;
+    if (!on_device) {
+        int r = ensure_dense(h);
+        if (r != KLB_OK) return r;
+        dst = h->fdense_dev;
+    }
+    cudaError_t e = h->p.precision == KLB_FP64
+                        ? launch_get_f<double>(h->g, (const double*)h->buf[h->cur], dst, h->stream)
+                        : launch_get_f<float>(h->g, (const float*)h->buf[h->cur], dst, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "get_f kernel");
+    h->launches += 1;
+    if (!on_device)
+        CK(h, cudaMemcpyAsync(f, h->fdense_dev, sizeof(double) * NQ * (size_t)h->g.nx * h->g.ny,
+                              cudaMemcpyDeviceToHost, h->stream));
+    return klb_sync(h);
+}
+
+// one step: optional fused diagnostics of the input state, then ping-pong
+static int one_step(klb_t* h) {
+    double* parts = nullptr;
+    if (h->pending_sample) parts = h->diag_partials;
+    cudaError_t e;
+    const int src = h->cur, dst = 1 - h->cur;
+    if (h->p.precision == KLB_FP64)
+        e = launch_step<double>(h->map[src], h->cd, h->g, (double*)h->buf[dst], parts, h->err_dev, h->spin_limit,
+                                h->stream);
+    else
+        e = launch_step<float>(h->map[src], h->cf, h->g, (float*)h->buf[dst], parts, h->err_dev, h->spin_limit,
+                               h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "step kernel");
+    h->launches += 1;
+    if (parts) {
+        e = launch_diag_finalize(parts, h->nparts, h->diag_ring + 7 * (h->nsamples % h->cap), h->err_dev,
+                                 h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "diagnostics finalize");
+        h->launches += 1;
+        h->nsamples += 1;
+        h->pending_sample = false;
+    }
+    h->cur = dst;
+    h->steps += 1;
+    if (h->p.sample_every > 0 && h->steps % h->p.sample_every == 0) h->pending_sample = true;
+    return KLB_OK;
+}
+
+int klb_step(klb_t* h, int64_t n) {
+    if (!h) return KLB_E_INVAL;
+    if (n < 0) return fail(h, KLB_E_INVAL, "negative step count");
+    if (!h->initialized) return fail(h, KLB_E_STATE, "klb_step before klb_init_fields");
+    for (int64_t s = 0; s < n; ++s) {
+        int r = one_step(h);
+        if (r != KLB_OK) return r;
+    }
+    return KLB_OK;
+}
+
+// take the sample of the current state if it is due and no step has taken it
+static int flush_sample(klb_t* h) {
+    if (!h->pending_sample) return KLB_OK;
+    cudaError_t e = h->p.precision == KLB_FP64
+                        ? launch_diag_partials<double>(h->cd, h->g, (const double*)h->buf[h->cur],
+                                                       h->diag_partials, h->stream)
+                        : launch_diag_partials<float>(h->cf, h->g, (const float*)h->buf[h->cur],
+                                                      h->diag_partials, h->stream);
+    if (e == cudaSuccess)
+        e = launch_diag_finalize(h->diag_partials, h->nparts, h->diag_ring + 7 * (h->nsamples % h->cap),
+                                 h->err_dev, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "diagnostics kernels");
+    h->launches += 2;
+    h->nsamples += 1;
+    h->pending_sample = false;
+    return KLB_OK;
+}
+
+int klb_moments(klb_t* h, double* rho, double* ux, double* uy, double* T, int on_device) {
+    if (!h) return KLB_E_INVAL;
+    if (!h->initialized) return fail(h, KLB_E_STATE, "klb_moments before klb_init_fields");
+    const size_t n = (size_t)h->g.nx * h->g.ny;
+    double* dst[4] = {rho, ux, uy, T};
+    double* d[4];
+    for (int i = 0; i < 4; ++i) d[i] = on_device ? dst[i] : (dst[i] ? h->fields_dev + i * n : nullptr);
+    cudaError_t e = h->p.precision == KLB_FP64
+                        ? launch_fields<double>(h->cd, h->g, (const double*)h->buf[h->cur], d[0], d[1], d[2], d[3],
+                                                h->stream)
+                        : launch_fields<float>(h->cf, h->g, (const float*)h->buf[h->cur], d[0], d[1], d[2], d[3],
+                                               h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "fields kernel");
+    h->launches += 1;
+    if (!on_device)
+        for (int i = 0; i < 4; ++i)
+            if (dst[i]) CK(h, cudaMemcpyAsync(dst[i], d[i], n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    return klb_sync(h);
+}
+
+int klb_diagnostics(klb_t* h, double* out, int64_t cap, int64_t* count) {
+    if (!h || !count || (cap > 0 && !out)) return h ? fail(h, KLB_E_INVAL, "NULL argument") : KLB_E_INVAL;
+    if (!h->initialized) return fail(h, KLB_E_STATE, "klb_diagnostics before klb_init_fields");
+    int r = flush_sample(h);
+    if (r != KLB_OK) return r;
+    const int64_t avail = std::min<int64_t>(h->nsamples, h->cap);
+    const int64_t m = std::min<int64_t>(avail, cap);
+    const int64_t first = h->nsamples - avail;  // oldest retained sample
+    for (int64_t i = 0; i < m; ++i) {
+        const int64_t slot = (first + i) % h->cap;
+        CK(h, cudaMemcpyAsync(out + 7 * i, h->diag_ring + 7 * slot, 7 * sizeof(double), cudaMemcpyDeviceToHost,
+                              h->stream));
+    }
+    *count = m;
+    return klb_sync(h);
+}
+
+int64_t klb_step_count(const klb_t* h) { return h ? h->steps : -1; }
+
+int64_t klb_launch_count(const klb_t* h) { return h ? h->launches : -1; }
+
+int klb_debug_set_spin_limit(klb_t* h, int64_t polls) {
+    if (!h || polls < 1) return KLB_E_INVAL;
+    h->spin_limit = polls;
+    return KLB_OK;
+}
+
+int klb_layout(const klb_t* h, const void** base, int64_t* pitch, int64_t* plane, int32_t* gx, int32_t* gy) {
+    if (!h) return KLB_E_INVAL;
+    if (base) *base = h->buf[h->cur];
+    if (pitch) *pitch = h->g.px;
+    if (plane) *plane = h->g.plane;
+    if (gx) *gx = GX;
+    if (gy) *gy = GY;
+    return KLB_OK;
+}
+
+const char* klb_last_error(const klb_t* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+// ---------------------------------------------------------------------------
+// checkpoint / resume
+// ---------------------------------------------------------------------------
+struct SaveHeader {
+    char magic[8];
+    int32_t version, nx, ny, precision;
+    int64_t steps, nsamples;
+    int32_t cap, pending;
+    klb_params p;
+};
+
+int klb_save(klb_t* h, const char* path) {
+    if (!h || !path) return KLB_E_INVAL;
+    if (!h->initialized) return fail(h, KLB_E_STATE, "klb_save before klb_init_fields");
+    int r = flush_sample(h);
+    if (r != KLB_OK) return r;
+    r = klb_sync(h);
+    if (r != KLB_OK) return r;
+    const size_t fbytes = (size_t)NQ * h->g.plane * h->esize;
+    std::string blob(fbytes, '\0');
+    std::string ring(sizeof(double) * 7 * h->cap, '\0');
+    CK(h, cudaMemcpy(&blob[0], h->buf[h->cur], fbytes, cudaMemcpyDeviceToHost));
+    CK(h, cudaMemcpy(&ring[0], h->diag_ring, ring.size(), cudaMemcpyDeviceToHost));
+    SaveHeader hd{};
+    memcpy(hd.magic, "KLBSAVE1", 8);
+    hd.version = 1;
+    hd.nx = h->g.nx;
+    hd.ny = h->g.ny;
+    hd.precision = h->p.precision;
+    hd.steps = h->steps;
+    hd.nsamples = h->nsamples;
+    hd.cap = h->cap;
+    hd.pending = h->pending_sample;
+    hd.p = h->p;
+    hd.p.stream = nullptr;
+    FILE* fp = fopen(path, "wb");
+    if (!fp) return fail(h, KLB_E_IO, std::string("cannot open ") + path);
+    bool ok = fwrite(&hd, sizeof(hd), 1, fp) == 1 && fwrite(ring.data(), 1, ring.size(), fp) == ring.size() &&
+              fwrite(blob.data(), 1, blob.size(), fp) == blob.size();
+    ok = (fclose(fp) == 0) && ok;
+    return ok ? KLB_OK : fail(h, KLB_E_IO, std::string("write failed: ") + path);
+}
+
+int klb_load(klb_t* h, const char* path) {
+    if (!h || !path) return KLB_E_INVAL;
+    FILE* fp = fopen(path, "rb");
+    if (!fp) return fail(h, KLB_E_IO, std::string("cannot open ") + path);
+    SaveHeader hd{};
+    if (fread(&hd, sizeof(hd), 1, fp) != 1 || memcmp(hd.magic, "KLBSAVE1", 8) != 0) {
+        fclose(fp);
+        return fail(h, KLB_E_IO, "not a klb checkpoint");
+    }
+    if (hd.nx != h->g.nx || hd.ny != h->g.ny || hd.precision != h->p.precision || hd.cap != h->cap) {
+        fclose(fp);
+        return fail(h, KLB_E_INVAL, "checkpoint does not match the handle (nx, ny, precision, diag capacity)");
+    }
+    const size_t fbytes = (size_t)NQ * h->g.plane * h->esize;
+    std::string blob(fbytes, '\0');
+    std::string ring(sizeof(double) * 7 * h->cap, '\0');
+    bool ok = fread(&ring[0], 1, ring.size(), fp) == ring.size() && fread(&blob[0], 1, blob.size(), fp) == blob.size();
+    fclose(fp);
+    if (!ok) return fail(h, KLB_E_IO, "truncated checkpoint");
+    CK(h, cudaStreamSynchronize(h->stream));
+    CK(h, cudaMemcpy(h->buf[0], blob.data(), fbytes, cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->buf[1], blob.data(), fbytes, cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->diag_ring, ring.data(), ring.size(), cudaMemcpyHostToDevice));
+    h->cur = 0;
+    h->steps = hd.steps;
+    h->nsamples = hd.nsamples;
+    h->pending_sample = hd.pending != 0;
+    h->initialized = true;
+    return KLB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,47 @@
+// klb_launch.h -- host-side declarations shared by the kernel files and the
+// C ABI implementation (not part of the public interface).
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "klb_device.cuh"
+
+namespace fdlb {
+
+// Polls granted to the second, draining wait after a bounded wait ran out.
+constexpr long long kDrainPolls = 1ll << 22;
+// Default poll budget of the tile-load wait.
+constexpr long long kDefaultSpin = 1ll << 22;
+
+template <typename T>
+cudaError_t launch_step(const CUtensorMap& in_map, const StepConst<T>& c, const Geom& g, T* out,
+                        double* diag_partials, int* err, long long spin_limit, cudaStream_t stream);
+template <typename T>
+size_t step_smem_bytes();
+void step_tile_shape(int precision, int* tx, int* ty);
+
+// f := f^(0)(fields) on the interior, with ghost images (klb_aux.cu).
+template <typename T>
+cudaError_t launch_init_feq(const StepConst<T>& c, const Geom& g, const double* rho, const double* ux,
+                            const double* uy, const double* Tm, T* out_a, T* out_b, cudaStream_t s);
+// Fixed-equilibrium ghosts of both buffers from the edge nodes of the fields.
+template <typename T>
+cudaError_t launch_fixed_ghosts(const StepConst<T>& c, const Geom& g, const double* rho, const double* ux,
+                                const double* uy, const double* Tm, T* out_a, T* out_b, cudaStream_t s);
+// interior f from / to a dense double array [19][ny][nx]
+template <typename T>
+cudaError_t launch_set_f(const Geom& g, const double* src, T* dst, cudaStream_t s);
+template <typename T>
+cudaError_t launch_get_f(const Geom& g, const T* src, double* dst, cudaStream_t s);
+// macroscopic fields of the interior
+template <typename T>
+cudaError_t launch_fields(const StepConst<T>& c, const Geom& g, const T* f, double* rho, double* ux, double* uy,
+                          double* Tm, cudaStream_t s);
+// stand-alone diagnostics partials of a state (same tiles and order as the fused path)
+template <typename T>
+cudaError_t launch_diag_partials(const StepConst<T>& c, const Geom& g, const T* f, double* partials,
+                                 cudaStream_t s);
+// reduce nparts partial records into ring slot `out` (7 doubles); sets ERR_NONFINITE
+cudaError_t launch_diag_finalize(const double* partials, int nparts, double* out, int* err, cudaStream_t s);
+
+}  // namespace fdlb

@@ -1,0 +1,218 @@
+"""Thin ctypes binding of libklb.so (include/klb.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  Arrays may be numpy float64 arrays (host memory) or torch
+float64 CUDA tensors (device memory, passed by pointer with on_device = 1).
+The library must have been built (paper_1010_4124_gb300/build.py, or
+__graft_entry__.build()); loading fails loudly otherwise -- there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libklb.so")
+
+KLB_OK = 0
+ERRORS = {-1: "KLB_E_INVAL", -2: "KLB_E_NOMEM", -3: "KLB_E_CUDA", -4: "KLB_E_NONFINITE",
+          -5: "KLB_E_DEVICE_TIMEOUT", -6: "KLB_E_STATE", -7: "KLB_E_IO"}
+BC = {"periodic": 0, "outflow": 1, "fixed_eq": 2}
+PREC = {"fp32": 0, "fp64": 1}
+
+
+class KlbError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class klb_params(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int32), ("ny", C.c_int32),
+        ("dx", C.c_double), ("dy", C.c_double), ("dt", C.c_double), ("tau", C.c_double),
+        ("v", C.c_double * 3),
+        ("bc_x_lo", C.c_int32), ("bc_x_hi", C.c_int32), ("bc_y_lo", C.c_int32), ("bc_y_hi", C.c_int32),
+        ("precision", C.c_int32), ("sample_every", C.c_int32), ("diag_capacity", C.c_int32),
+        ("eps", C.c_double),
+        ("stream", C.c_void_p),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    """Load libklb.so (raises if it is missing: no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run paper_1010_4124_gb300/build.py")
+        L = C.CDLL(LIB_PATH)
+        vp, i64, i32 = C.c_void_p, C.c_int64, C.c_int32
+        P = C.POINTER(klb_params)
+        sig = {
+            "klb_params_default": (None, [P]),
+            "klb_create": (C.c_int, [P, C.POINTER(vp)]),
+            "klb_destroy": (None, [vp]),
+            "klb_init_fields": (C.c_int, [vp, vp, vp, vp, vp, C.c_int]),
+            "klb_set_f": (C.c_int, [vp, vp, C.c_int]),
+            "klb_get_f": (C.c_int, [vp, vp, C.c_int]),
+            "klb_step": (C.c_int, [vp, i64]),
+            "klb_sync": (C.c_int, [vp]),
+            "klb_moments": (C.c_int, [vp, vp, vp, vp, vp, C.c_int]),
+            "klb_diagnostics": (C.c_int, [vp, vp, i64, C.POINTER(i64)]),
+            "klb_step_count": (i64, [vp]),
+            "klb_save": (C.c_int, [vp, C.c_char_p]),
+            "klb_load": (C.c_int, [vp, C.c_char_p]),
+            "klb_last_error": (C.c_char_p, [vp]),
+            "klb_layout": (C.c_int, [vp, C.POINTER(vp), C.POINTER(i64), C.POINTER(i64), C.POINTER(i32),
+                                     C.POINTER(i32)]),
+            "klb_launch_count": (i64, [vp]),
+            "klb_debug_set_spin_limit": (C.c_int, [vp, i64]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(h, code):
+    if code != KLB_OK:
+        msg = lib().klb_last_error(h)
+        raise KlbError(code, msg.decode() if msg else "")
+
+
+def _ptr(a):
+    """(pointer, on_device) of a numpy array or a torch tensor (float64, contiguous)."""
+    if a is None:
+        return None, 0
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError("numpy arrays must be C-contiguous float64")
+        return a.ctypes.data, 0
+    # torch tensor
+    if str(a.dtype) != "torch.float64" or not a.is_contiguous():
+        raise TypeError("tensors must be contiguous float64")
+    return a.data_ptr(), 1 if a.is_cuda else 0
+
+
+def make_params(nx, ny, dx, dy, dt, tau, v=(1.0, 2.0, 3.0), bc_x=("periodic", "periodic"),
+                bc_y=("periodic", "periodic"), precision="fp32", sample_every=0, diag_capacity=0,
+                eps=1e-6, stream=None) -> klb_params:
+    p = klb_params()
+    lib().klb_params_default(C.byref(p))
+    p.nx, p.ny, p.dx, p.dy, p.dt, p.tau = nx, ny, dx, dy, dt, tau
+    p.v = (C.c_double * 3)(*v)
+    p.bc_x_lo, p.bc_x_hi = BC[bc_x[0]], BC[bc_x[1]]
+    p.bc_y_lo, p.bc_y_hi = BC[bc_y[0]], BC[bc_y[1]]
+    p.precision = PREC[precision]
+    p.sample_every = sample_every
+    p.diag_capacity = diag_capacity
+    p.eps = eps
+    p.stream = stream
+    return p
+
+
+class Klb:
+    """One simulation handle (klb_create ... klb_destroy)."""
+
+    def __init__(self, params: klb_params):
+        h = C.c_void_p()
+        code = lib().klb_create(C.byref(params), C.byref(h))
+        if code != KLB_OK:
+            raise KlbError(code, (lib().klb_last_error(None) or b"").decode())
+        self.h = h
+        self.nx, self.ny = params.nx, params.ny
+        self.params = params
+
+    @classmethod
+    def from_problem(cls, pb, precision="fp32", stream=None, **kw):
+        return cls(make_params(pb.nx, pb.ny, pb.dx, pb.dy, pb.dt, pb.tau, v=pb.v, bc_x=pb.bc_x, bc_y=pb.bc_y,
+                               precision=precision, sample_every=kw.pop("sample_every", pb.sample_every),
+                               stream=stream, **kw))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().klb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # --- entry points ------------------------------------------------------
+    def init_fields(self, rho, ux, uy, T):
+        ptrs = [_ptr(a) for a in (rho, ux, uy, T)]
+        ond = {p[1] for p in ptrs}
+        if len(ond) != 1:
+            raise TypeError("all four fields must live on the same side (host or device)")
+        _check(self.h, lib().klb_init_fields(self.h, *[p[0] for p in ptrs], ond.pop()))
+
+    def set_f(self, f):
+        p, d = _ptr(f)
+        _check(self.h, lib().klb_set_f(self.h, p, d))
+
+    def get_f(self, out=None):
+        if out is None:
+            out = np.empty((19, self.ny, self.nx))
+        p, d = _ptr(out)
+        _check(self.h, lib().klb_get_f(self.h, p, d))
+        return out
+
+    def step(self, n: int = 1):
+        _check(self.h, lib().klb_step(self.h, int(n)))
+
+    def sync(self):
+        _check(self.h, lib().klb_sync(self.h))
+
+    def moments(self, out=None):
+        if out is None:
+            out = tuple(np.empty((self.ny, self.nx)) for _ in range(4))
+        ptrs = [_ptr(a) for a in out]
+        ond = {p[1] for p in ptrs if p[0] is not None}
+        _check(self.h, lib().klb_moments(self.h, *[p[0] for p in ptrs], ond.pop() if ond else 0))
+        return out
+
+    def diagnostics(self, cap: int = 1 << 16):
+        out = np.zeros((cap, 7))
+        cnt = C.c_int64(0)
+        _check(self.h, lib().klb_diagnostics(self.h, out.ctypes.data, cap, C.byref(cnt)))
+        return out[: cnt.value].copy()
+
+    @property
+    def step_count(self) -> int:
+        return int(lib().klb_step_count(self.h))
+
+    @property
+    def launch_count(self) -> int:
+        return int(lib().klb_launch_count(self.h))
+
+    def save(self, path: str):
+        _check(self.h, lib().klb_save(self.h, path.encode()))
+
+    def load(self, path: str):
+        _check(self.h, lib().klb_load(self.h, path.encode()))
+
+    def layout(self):
+        base, pitch, plane = C.c_void_p(), C.c_int64(), C.c_int64()
+        gx, gy = C.c_int32(), C.c_int32()
+        _check(self.h, lib().klb_layout(self.h, C.byref(base), C.byref(pitch), C.byref(plane), C.byref(gx),
+                                        C.byref(gy)))
+        return base.value, pitch.value, plane.value, gx.value, gy.value
+
+    def debug_set_spin_limit(self, polls: int):
+        _check(self.h, lib().klb_debug_set_spin_limit(self.h, int(polls)))

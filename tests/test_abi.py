@@ -1,0 +1,70 @@
+"""The C-ABI library builds, loads and exports every entry point declared in
+include/klb.h (no compute calls: this runs without a GPU)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared(header):
+    txt = open(os.path.join(ROOT, "include", header)).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(klb_\w+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1010_4124_gb300 import build
+    path = build.build()
+    return C.CDLL(path)
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared("klb.h")
+    assert len(names) >= 15
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_params_default_is_host_only(lib):
+    from paper_1010_4124_gb300 import klb
+    p = klb.klb_params()
+    klb.lib().klb_params_default(C.byref(p))
+    assert tuple(p.v) == (1.0, 2.0, 3.0)
+    assert p.eps == 1e-6 and p.precision == 0 and p.stream is None
+
+
+def test_params_struct_layout_matches_header(lib):
+    # the ctypes mirror must have the same size as the C struct: compile a
+    # probe with the host compiler against include/klb.h
+    import subprocess
+    import tempfile
+    from paper_1010_4124_gb300 import klb
+    src = '#include "klb.h"\n#include <stdio.h>\n#include <stddef.h>\nint main(void){printf("%zu %zu\\n", sizeof(klb_params), offsetof(klb_params, stream));return 0;}\n'
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "p.c")
+        open(c, "w").write(src)
+        exe = os.path.join(d, "p")
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        size, off = map(int, subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split())
+    assert C.sizeof(klb.klb_params) == size
+    assert klb.klb_params.stream.offset == off
+
+
+def test_create_rejects_bad_params_without_gpu(lib):
+    from paper_1010_4124_gb300 import klb
+    p = klb.make_params(0, 8, 0.01, 0.01, 1e-5, 1e-5)
+    with pytest.raises(klb.KlbError) as e:
+        klb.Klb(p)
+    assert e.value.code == -1
+    p = klb.make_params(8, 8, 0.01, 0.01, 1e-5, 1e-5, bc_x=("periodic", "outflow"))
+    with pytest.raises(klb.KlbError) as e:
+        klb.Klb(p)
+    assert e.value.code == -1
+    p = klb.make_params(8, 8, 0.01, 0.01, 1e-5, 1e-5, v=(1.0, 1.0, 3.0))
+    with pytest.raises(klb.KlbError) as e:
+        klb.Klb(p)
+    assert e.value.code == -1

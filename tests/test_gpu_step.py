@@ -1,0 +1,255 @@
+"""Parity of the CUDA step (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (max norm, relative to each field's or plane's max norm):
+FP64 <= 1e-12 per field after any number of steps; FP32 (arithmetic in FP32,
+diagnostics in FP64) <= 1e-5 on rho, u, T after 1000 steps of smooth data.
+"""
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+from gpu_common import gpu_handle, oracle_params, perturbed_state, rel_err_fields, rel_err_planes
+from oracle import core
+from paper_1010_4124_gb300 import inputs, klb
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 1e-5
+
+
+def _problem(nx, ny, bcx, bcy, dt=2e-5, tau=4e-5, dx=0.01, dy=0.012):
+    return inputs.Problem("custom", nx, ny, dx, dy, dt, tau, 1, bc_x=(bcx, bcx), bc_y=(bcy, bcy))
+
+
+BCS = [("periodic", "periodic"), ("periodic", "outflow"), ("outflow", "periodic"), ("fixed_eq", "outflow"),
+       ("outflow", "fixed_eq"), ("fixed_eq", "fixed_eq")]
+SIZES = [(70, 37), (32, 8), (5, 3), (1, 1), (97, 130)]
+
+
+@pytest.mark.parametrize("bcx,bcy", BCS)
+@pytest.mark.parametrize("nx,ny", SIZES)
+def test_fp64_one_step_parity(nx, ny, bcx, bcy):
+    pb = _problem(nx, ny, bcx, bcy)
+    p = oracle_params(pb)
+    fields = inputs.rough_random_fields(nx, ny, seed=nx * 1000 + ny)
+    f0 = perturbed_state(pb, fields, seed=3)
+    fixed = core.fixed_ghosts(p, *fields)
+    ref = core.step(p, f0, fixed=fixed)
+    with gpu_handle(pb, "fp64") as h:
+        h.init_fields(*[np.ascontiguousarray(a) for a in fields])
+        h.set_f(np.ascontiguousarray(f0))
+        h.step(1)
+        got = h.get_f()
+    assert rel_err_planes(got, ref) <= TOL64
+
+
+@pytest.mark.parametrize("bcx,bcy", BCS[:4])
+def test_fp64_many_steps_parity(bcx, bcy):
+    pb = _problem(67, 45, bcx, bcy)
+    p = oracle_params(pb)
+    fields = inputs.smooth_random_fields(67, 45, seed=8, amp=0.08)
+    f0 = perturbed_state(pb, fields, seed=4, amp=0.02)
+    fixed = core.fixed_ghosts(p, *fields)
+    ref, _ = core.run(p, f0, 60, fixed=fixed)
+    with gpu_handle(pb, "fp64") as h:
+        h.init_fields(*[np.ascontiguousarray(a) for a in fields])
+        h.set_f(np.ascontiguousarray(f0))
+        h.step(60)
+        got = h.get_f()
+    errs = rel_err_fields(got, ref, p)
+    assert max(errs.values()) <= TOL64, errs
+
+
+def test_sod_fp64_full_run():
+    # config: Sod tube 200 x 4, dt = tau = 2e-5, 5000 steps to t = 0.1
+    pb = inputs.sod(200, 4, 5000)
+    p = oracle_params(pb)
+    fields = inputs.fields(pb)
+    f0 = core.init_feq(p, *fields)
+    ref, _ = core.run(p, f0, pb.steps, fixed=core.fixed_ghosts(p, *fields))
+    with gpu_handle(pb, "fp64") as h:
+        h.init_fields(*fields)
+        h.step(pb.steps)
+        got = h.get_f()
+        assert h.step_count == 5000
+    errs = rel_err_fields(got, ref, p)
+    assert max(errs.values()) <= TOL64, errs
+
+
+def test_fp32_smooth_1000_steps():
+    pb = inputs.khi(128, 128, 1000, Dv=4.0, Drho=4.0)
+    p = oracle_params(pb)
+    fields = inputs.fields(pb)
+    f0 = core.init_feq(p, *fields)
+    ref, _ = core.run(p, f0, 1000)
+    with gpu_handle(pb, "fp32") as h:
+        h.init_fields(*fields)
+        h.step(1000)
+        got = h.get_f()
+    errs = rel_err_fields(got, ref, p)
+    assert errs["rho"] <= TOL32 and errs["u"] <= TOL32 and errs["T"] <= TOL32, errs
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-4)])
+def test_diagnostics_series_parity(prec, tol):
+    pb = inputs.khi(64, 96, 200, Dv=4.0, Drho=4.0, sample_every=10)
+    p = oracle_params(pb)
+    fields = inputs.fields(pb)
+    f0 = core.init_feq(p, *fields)
+    _, dref = core.run(p, f0, pb.steps, sample_every=10)
+    with gpu_handle(pb, prec) as h:
+        h.init_fields(*fields)
+        h.step(pb.steps)
+        d = h.diagnostics()
+    assert d.shape == dref.shape == (21, 7)
+    for k in range(7):
+        scale = np.abs(dref[:, k]).max()
+        if k in (1, 2):  # momentum sums cancel to ~0: compare against the mass scale
+            scale = np.abs(dref[:, 0]).max()
+        assert np.abs(d[:, k] - dref[:, k]).max() <= tol * scale, k
+
+
+def test_conservation_fp64_periodic():
+    pb = _problem(80, 72, "periodic", "periodic")
+    fields = inputs.smooth_random_fields(80, 72, seed=2, amp=0.1)
+    f0 = perturbed_state(pb, fields, seed=9, amp=0.02)
+    with gpu_handle(pb, "fp64", sample_every=50) as h:
+        h.init_fields(*fields)
+        h.set_f(np.ascontiguousarray(f0))
+        h.step(200)
+        d = h.diagnostics()
+    # samples after 0, 50, ..., 200 steps; the first is taken after set_f
+    for k, scale in ((0, d[0, 0]), (1, d[0, 0]), (2, d[0, 0]), (3, d[0, 3])):
+        assert np.abs(d[:, k] - d[0, k]).max() <= 200 * 1e-14 * abs(scale), k
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 2e-6)])
+def test_khi512_full_size_step_parity(prec, tol):
+    # the 512 x 512 KHI at full size: after 200 GPU steps, one oracle step from
+    # the GPU state must equal the GPU's next step at every node
+    pb = inputs.khi(512, 512, 200)
+    p = oracle_params(pb)
+    with gpu_handle(pb, prec) as h:
+        h.init_fields(*inputs.fields(pb))
+        h.step(200)
+        fa = h.get_f()
+        h.step(1)
+        fb = h.get_f()
+    ref = core.step(p, fa)
+    assert rel_err_planes(fb, ref) <= tol
+
+
+def test_roofline_4096_windows_parity():
+    # the 4096 x 4096 four-mode KHI in FP32: windows of the GPU state after 20
+    # steps; one oracle step on each window (periodic wrap, then the 3-node rim
+    # discarded) equals the GPU's next step on the window's core
+    pb = inputs.roofline_4096(20)
+    rng = np.random.default_rng(12)
+    with gpu_handle(pb, "fp32") as h:
+        h.init_fields(*inputs.fields(pb))
+        h.step(20)
+        fa = h.get_f()
+        h.step(1)
+        fb = h.get_f()
+    W = 40
+    corners = [(0, 0), (4096 - W, 4096 - W), (2048 - W // 2, 2048 - W // 2)] + \
+        [tuple(rng.integers(0, 4096 - W, 2)) for _ in range(3)]
+    for (y0, x0) in corners:
+        ys = np.arange(y0 - 3, y0 + W + 3)
+        xs = np.arange(x0 - 3, x0 + W + 3) % 4096
+        win = fa[:, :, xs]
+        # rows: inside the domain use the state, beyond it the outflow copy
+        win = win[:, np.clip(ys, 0, 4095), :]
+        pw = core.Params(nx=W + 6, ny=W + 6, dx=pb.dx, dy=pb.dy, dt=pb.dt, tau=pb.tau,
+                         bc_x=("periodic", "periodic"), bc_y=("periodic", "periodic"))
+        ref = core.step(pw, win)[:, 3:-3, 3:-3]
+        got = fb[:, y0:y0 + W, x0:x0 + W]
+        assert rel_err_planes(got, ref) <= 2e-6, (y0, x0)
+
+
+def test_step_before_init_and_bad_args():
+    pb = _problem(16, 16, "periodic", "periodic")
+    with gpu_handle(pb, "fp32") as h:
+        with pytest.raises(klb.KlbError) as e:
+            h.step(1)
+        assert e.value.code == -6
+        h.init_fields(*inputs.smooth_random_fields(16, 16, 0))
+        with pytest.raises(klb.KlbError) as e:
+            h.step(-1)
+        assert e.value.code == -1
+
+
+def test_bounded_wait_runs_out_and_context_survives():
+    # fault injection on the host: a poll budget of 1 makes the tile-load wait
+    # run out; the kernel reports KLB_E_DEVICE_TIMEOUT and exits cleanly
+    pb = _problem(64, 48, "periodic", "outflow")
+    fields = inputs.smooth_random_fields(64, 48, 1)
+    with gpu_handle(pb, "fp32") as h:
+        h.init_fields(*fields)
+        h.debug_set_spin_limit(1)
+        h.step(3)
+        with pytest.raises(klb.KlbError) as e:
+            h.sync()
+        assert e.value.code == -5
+        # the context is still usable: a fresh handle steps normally
+    with gpu_handle(pb, "fp64") as h2:
+        h2.init_fields(*fields)
+        h2.step(2)
+        h2.sync()
+        p = oracle_params(pb)
+        ref, _ = core.run(p, core.init_feq(p, *fields), 2)
+        assert rel_err_planes(h2.get_f(), ref) <= TOL64
+
+
+def test_nonfinite_state_is_reported():
+    pb = _problem(40, 40, "periodic", "periodic")
+    fields = [np.array(a) for a in inputs.smooth_random_fields(40, 40, 1)]
+    fields[0][7, 11] = np.nan  # a NaN planted in the initial density
+    pb.sample_every = 1
+    with gpu_handle(pb, "fp32") as h:
+        h.init_fields(*fields)
+        h.step(2)
+        with pytest.raises(klb.KlbError) as e:
+            h.diagnostics()
+        assert e.value.code == -4
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_save_load_resumes_bitwise(prec):
+    pb = inputs.khi(96, 80, 40, sample_every=10)
+    fields = inputs.fields(pb)
+    with gpu_handle(pb, prec) as a:
+        a.init_fields(*fields)
+        a.step(40)
+        fa, da = a.get_f(), a.diagnostics()
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "ck.klb")
+        with gpu_handle(pb, prec) as b:
+            b.init_fields(*fields)
+            b.step(20)
+            b.save(path)
+        with gpu_handle(pb, prec) as c:
+            c.load(path)
+            assert c.step_count == 20
+            c.step(20)
+            fc, dc = c.get_f(), c.diagnostics()
+    assert np.array_equal(fa, fc)
+    assert np.array_equal(da, dc)
+
+
+def test_device_pointer_fields_from_torch():
+    torch = pytest.importorskip("torch")
+    pb = inputs.khi(64, 64, 10)
+    fields = inputs.fields(pb)
+    dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in fields]
+    with gpu_handle(pb, "fp64") as h:
+        h.init_fields(*dev)
+        h.step(10)
+        out = tuple(torch.empty((64, 64), dtype=torch.float64, device="cuda") for _ in range(4))
+        h.moments(out)
+        host = h.moments()
+    for a, b in zip(out, host):
+        assert np.array_equal(a.cpu().numpy(), b)
