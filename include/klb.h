@@ -155,12 +155,14 @@ int klb_layout(const klb_t* h, const void** base, int64_t* pitch, int64_t* plane
  * library launched on its stream). */
 int64_t klb_launch_count(const klb_t* h);
 
-/* Fault injection for tests: the number of polls each step-kernel CTA grants
- * its bounded wait on the shared-memory tile load (default 2^22).  With a
- * small value the wait runs out, the kernel records KLB_E_DEVICE_TIMEOUT
- * (reported by the next synchronising call), lets the copy in flight land and
- * exits without computing; the context stays usable.  polls >= 1. */
-int klb_debug_set_spin_limit(klb_t* h, int64_t polls);
+/* Fault injection for tests.  With polls > 0, every later step launch also
+ * waits, with a budget of `polls` polls, on a device barrier that nothing
+ * arrives on (a flag that nothing sets): the wait runs out, each CTA records
+ * KLB_E_DEVICE_TIMEOUT (reported by the next synchronising call), lets its
+ * tile copy in flight land and exits without computing, and the CUDA context
+ * stays usable.  polls = 0 switches the injection off.  The state of a step
+ * that ran under injection is undefined. */
+int klb_debug_inject_wait_timeout(klb_t* h, int64_t polls);
 
 #ifdef __cplusplus
 }

@@ -53,7 +53,9 @@ def build(force: bool = False, verbose: bool = False, extra: list | None = None)
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj]
+        # FP64 parity translation units round every multiply and add separately
+        per_file = ["-fmad=false"] if src.endswith("_f64.cu") else []
+        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *per_file, *extra, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")

@@ -1,8 +1,9 @@
-// klb_aux.cu -- small kernels around the step: initial equilibrium state,
+// klb_aux.cuh -- small kernels around the step (templates; klb_aux_f32.cu and
+// klb_aux_f64.cu instantiate them): initial equilibrium state,
 // fixed-equilibrium ghosts, distribution import / export, macroscopic fields,
-// and the diagnostics reduction.  All of them are elementwise or single-pass
-// reductions; none is on the per-step hot path except the diagnostics
-// finalisation (one tiny launch per sample).
+// and the diagnostics partials.  All are elementwise or single-pass
+// reductions; none is on the per-step hot path.
+#pragma once
 #include "klb_launch.h"
 
 namespace fdlb {
@@ -14,24 +15,13 @@ __global__ void init_feq_kernel(const StepConst<T> c, const Geom g, const double
                                 const double* __restrict__ ux, const double* __restrict__ uy,
                                 const double* __restrict__ Tm, T* __restrict__ a, T* __restrict__ b) {
     const long long n = (long long)g.nx * g.ny;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
         const int ix = (int)(k % g.nx), iy = (int)(k / g.nx);
-        NodeEq<T> s;
-        s.rho = T(rho[k]);
-        s.ux = T(ux[k]);
-        s.uy = T(uy[k]);
-        s.Tm = T(Tm[k]);
-        T iT = T(1) / s.Tm;
-        T u2 = s.ux * s.ux + s.uy * s.uy;
-        s.A = T(1) - T(0.5) * u2 * iT;
-        s.a = s.ux * iT;
-        s.b = s.uy * iT;
-        T F[4];
-        global_coeffs(c, s.Tm, F);
-        for (int j = 0; j < 4; ++j) s.rF[j] = s.rho * F[j];
-#pragma unroll
+        const NodeEq<T> s = Arith<T>::from_moments(c, T(rho[k]), T(ux[k]), T(uy[k]), T(Tm[k]));
+#pragma unroll 1
         for (int q = 0; q < NQ; ++q) {
-            T v = feq_q(c, s, q);
+            const T v = Arith<T>::feq(c, s, q);
             store_with_images(a, g, q, ix, iy, v);
             store_with_images(b, g, q, ix, iy, v);
         }
@@ -54,28 +44,17 @@ __global__ void fixed_ghosts_kernel(const StepConst<T> c, const Geom g, const do
             ix = side == 0 ? 0 : g.nx - 1;
             if ((side == 0 ? g.bcx_lo : g.bcx_hi) != 2) continue;
         } else {
-            int u = t - 2 * g.ny;
+            const int u = t - 2 * g.ny;
             side = u < g.nx ? 2 : 3;
             ix = u % g.nx;
             iy = side == 2 ? 0 : g.ny - 1;
             if ((side == 2 ? g.bcy_lo : g.bcy_hi) != 2) continue;
         }
         const long long k = (long long)iy * g.nx + ix;
-        NodeEq<T> s;
-        s.rho = T(rho[k]);
-        s.ux = T(ux[k]);
-        s.uy = T(uy[k]);
-        s.Tm = T(Tm[k]);
-        T iT = T(1) / s.Tm;
-        T u2 = s.ux * s.ux + s.uy * s.uy;
-        s.A = T(1) - T(0.5) * u2 * iT;
-        s.a = s.ux * iT;
-        s.b = s.uy * iT;
-        T F[4];
-        global_coeffs(c, s.Tm, F);
-        for (int j = 0; j < 4; ++j) s.rF[j] = s.rho * F[j];
+        const NodeEq<T> s = Arith<T>::from_moments(c, T(rho[k]), T(ux[k]), T(uy[k]), T(Tm[k]));
+#pragma unroll 1
         for (int q = 0; q < NQ; ++q) {
-            T v = feq_q(c, s, q);
+            const T v = Arith<T>::feq(c, s, q);
             for (int d = 1; d <= 3; ++d) {
                 long long off;
                 if (side == 0) off = (long long)(iy + GY) * g.px + (GX - d);
@@ -92,7 +71,8 @@ __global__ void fixed_ghosts_kernel(const StepConst<T> c, const Geom g, const do
 template <typename T>
 __global__ void set_f_kernel(const Geom g, const double* __restrict__ src, T* __restrict__ dst) {
     const long long n = (long long)g.nx * g.ny;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < NQ * n; k += (long long)gridDim.x * blockDim.x) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < NQ * n;
+         k += (long long)gridDim.x * blockDim.x) {
         const int q = (int)(k / n);
         const long long r = k % n;
         store_with_images(dst, g, q, (int)(r % g.nx), (int)(r / g.nx), T(src[k]));
@@ -102,7 +82,8 @@ __global__ void set_f_kernel(const Geom g, const double* __restrict__ src, T* __
 template <typename T>
 __global__ void get_f_kernel(const Geom g, const T* __restrict__ src, double* __restrict__ dst) {
     const long long n = (long long)g.nx * g.ny;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < NQ * n; k += (long long)gridDim.x * blockDim.x) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < NQ * n;
+         k += (long long)gridDim.x * blockDim.x) {
         const int q = (int)(k / n);
         const long long r = k % n;
         const int ix = (int)(r % g.nx), iy = (int)(r / g.nx);
@@ -115,12 +96,13 @@ __global__ void fields_kernel(const StepConst<T> c, const Geom g, const T* __res
                               double* __restrict__ rho, double* __restrict__ ux, double* __restrict__ uy,
                               double* __restrict__ Tm) {
     const long long n = (long long)g.nx * g.ny;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
         const int ix = (int)(k % g.nx), iy = (int)(k / g.nx);
         T fl[NQ];
 #pragma unroll
         for (int q = 0; q < NQ; ++q) fl[q] = f[q * g.plane + (long long)(iy + GY) * g.px + (ix + GX)];
-        NodeEq<T> s = node_state(c, fl);
+        const NodeEq<T> s = Arith<T>::node_state(c, fl);
         if (rho) rho[k] = s.rho;
         if (ux) ux[k] = s.ux;
         if (uy) uy[k] = s.uy;
@@ -140,45 +122,13 @@ __global__ void __launch_bounds__(TX* TY) diag_partials_kernel(const StepConst<T
     T fl[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) fl[q] = active ? f[q * g.plane + (long long)(iy + GY) * g.px + (ix + GX)] : T(1);
-    NodeEq<T> s = node_state(c, fl);
+    const NodeEq<T> s = Arith<T>::node_state(c, fl);
     double v[8];
     node_diag(s, active, v);
     diag_block_reduce<TX * TY>(v, partials + 8ll * (blockIdx.y * gridDim.x + blockIdx.x));
 }
 
-// One block folds all partial records, in record order per thread and a fixed
-// tree across threads.
-__global__ void diag_finalize_kernel(const double* __restrict__ partials, int nparts, double* __restrict__ out,
-                                     int* __restrict__ err) {
-    __shared__ double red[256][8];
-    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            double x = partials[8ll * i + k];
-            acc[k] = (k == 4 || k == 5 || k == 7) ? fmax(acc[k], x) : acc[k] + x;
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < 8; ++k) red[threadIdx.x][k] = acc[k];
-    __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-        if (threadIdx.x < w) {
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                double x = red[threadIdx.x + w][k];
-                red[threadIdx.x][k] = (k == 4 || k == 5 || k == 7) ? fmax(red[threadIdx.x][k], x) : red[threadIdx.x][k] + x;
-            }
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        for (int k = 0; k < 7; ++k) out[k] = red[0][k];
-        if (red[0][7] != 0.0) atomicOr(err, ERR_NONFINITE);
-    }
-}
-
-static int grid_for(long long n, int threads) {
+static inline int grid_for(long long n, int threads) {
     long long b = (n + threads - 1) / threads;
     if (b < 1) b = 1;
     if (b > 152 * 64) b = 152 * 64;
@@ -213,24 +163,15 @@ cudaError_t launch_fields(const StepConst<T>& c, const Geom& g, const T* f, doub
     fields_kernel<T><<<grid_for((long long)g.nx * g.ny, 256), 256, 0, s>>>(c, g, f, rho, ux, uy, Tm);
     return cudaGetLastError();
 }
-template <typename T>
-cudaError_t launch_diag_partials(const StepConst<T>& c, const Geom& g, const T* f, double* partials,
-                                 cudaStream_t s) {
-    int TX, TY;
-    step_tile_shape(sizeof(T) == 8 ? 1 : 0, &TX, &TY);
+template <typename T, int TX, int TY>
+cudaError_t launch_diag_partials_tiles(const StepConst<T>& c, const Geom& g, const T* f, double* partials,
+                                       cudaStream_t s) {
     dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY);
-    if (sizeof(T) == 8)
-        diag_partials_kernel<T, 32, 8><<<grid, 256, 0, s>>>(c, g, f, partials);
-    else
-        diag_partials_kernel<T, 32, 16><<<grid, 512, 0, s>>>(c, g, f, partials);
-    return cudaGetLastError();
-}
-cudaError_t launch_diag_finalize(const double* partials, int nparts, double* out, int* err, cudaStream_t s) {
-    diag_finalize_kernel<<<1, 256, 0, s>>>(partials, nparts, out, err);
+    diag_partials_kernel<T, TX, TY><<<grid, TX * TY, 0, s>>>(c, g, f, partials);
     return cudaGetLastError();
 }
 
-#define KLB_INST(T)                                                                                              \
+#define KLB_AUX_INST(T, TX, TY)                                                                                  \
     template cudaError_t launch_init_feq<T>(const StepConst<T>&, const Geom&, const double*, const double*,     \
                                             const double*, const double*, T*, T*, cudaStream_t);              \
     template cudaError_t launch_fixed_ghosts<T>(const StepConst<T>&, const Geom&, const double*, const double*, \
@@ -239,8 +180,10 @@ cudaError_t launch_diag_finalize(const double* partials, int nparts, double* out
     template cudaError_t launch_get_f<T>(const Geom&, const T*, double*, cudaStream_t);                         \
     template cudaError_t launch_fields<T>(const StepConst<T>&, const Geom&, const T*, double*, double*, double*, \
                                           double*, cudaStream_t);                                              \
-    template cudaError_t launch_diag_partials<T>(const StepConst<T>&, const Geom&, const T*, double*, cudaStream_t);
-KLB_INST(float)
-KLB_INST(double)
+    template <>                                                                                                  \
+    cudaError_t launch_diag_partials<T>(const StepConst<T>& c, const Geom& g, const T* f, double* partials,     \
+                                        cudaStream_t s) {                                                      \
+        return launch_diag_partials_tiles<T, TX, TY>(c, g, f, partials, s);                                    \
+    }
 
 }  // namespace fdlb

@@ -1,0 +1,47 @@
+// klb_aux_f32.cu -- FP32 instantiations of the auxiliary kernels, and the
+// diagnostics finalisation (precision independent).
+#include "klb_aux.cuh"
+
+namespace fdlb {
+
+KLB_AUX_INST(float, 32, 16)
+
+// One block folds all partial records, in record order per thread and a fixed
+// tree across threads.
+__global__ void diag_finalize_kernel(const double* __restrict__ partials, int nparts, double* __restrict__ out,
+                                     int* __restrict__ err) {
+    __shared__ double red[256][8];
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const double x = partials[8ll * i + k];
+            acc[k] = (k == 4 || k == 5 || k == 7) ? fmax(acc[k], x) : acc[k] + x;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) red[threadIdx.x][k] = acc[k];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const double x = red[threadIdx.x + w][k];
+                red[threadIdx.x][k] =
+                    (k == 4 || k == 5 || k == 7) ? fmax(red[threadIdx.x][k], x) : red[threadIdx.x][k] + x;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 7; ++k) out[k] = red[0][k];
+        if (red[0][7] != 0.0) atomicOr(err, ERR_NONFINITE);
+    }
+}
+
+cudaError_t launch_diag_finalize(const double* partials, int nparts, double* out, int* err, cudaStream_t s) {
+    diag_finalize_kernel<<<1, 256, 0, s>>>(partials, nparts, out, err);
+    return cudaGetLastError();
+}
+
+}  // namespace fdlb

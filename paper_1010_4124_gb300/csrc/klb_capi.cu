@@ -37,6 +37,7 @@ struct klb {
     bool own_stream = false;
     int64_t launches = 0;
     long long spin_limit = kDefaultSpin;
+    int inject = 0;
     std::string err;
 };
 
@@ -89,7 +90,46 @@ static void fill_const(const klb_params& p, StepConst<T>& c) {
         c.fk[k][0] = T(a1 * a2 / den);
         c.fk[k][1] = T(-4.0 * (a1 + a2) / den);
         c.fk[k][2] = T(24.0 / den);
+        c.a4[k] = T(4.0 * (a1 + a2));
+        c.pk[k] = T(a1 * a2);
+        c.den[k] = T(den);
     }
+    // inverse of the Gram matrix G_ab = sum_q B_aq B_bq, B = (1, v_x, v_y, |v|^2)
+    double B[4][NQ], G[4][8];
+    for (int q = 0; q < NQ; ++q) {
+        const double vx = double(c.vx[q]), vy = double(c.vy[q]);
+        B[0][q] = 1.0;
+        B[1][q] = vx;
+        B[2][q] = vy;
+        B[3][q] = vx * vx + vy * vy;
+    }
+    for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 8; ++b) {
+            G[a][b] = 0.0;
+            if (b < 4)
+                for (int q = 0; q < NQ; ++q) G[a][b] += B[a][q] * B[b][q];
+            else
+                G[a][b] = (b - 4 == a) ? 1.0 : 0.0;
+        }
+    for (int col = 0; col < 4; ++col) {  // Gauss-Jordan with partial pivoting
+        int piv = col;
+        for (int r = col + 1; r < 4; ++r)
+            if (std::fabs(G[r][col]) > std::fabs(G[piv][col])) piv = r;
+        for (int b = 0; b < 8; ++b) std::swap(G[col][b], G[piv][b]);
+        const double d = G[col][col];
+        for (int b = 0; b < 8; ++b) G[col][b] /= d;
+        for (int r = 0; r < 4; ++r)
+            if (r != col) {
+                const double m = G[r][col];
+                for (int b = 0; b < 8; ++b) G[r][b] -= m * G[col][b];
+            }
+    }
+    for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) c.ginv[a][b] = T(G[a][b + 4]);
+    c.dt = T(p.dt);
+    c.dx = T(p.dx);
+    c.dy = T(p.dy);
+    c.eps = T(eps);
     c.relax = T(p.dt / p.tau);
 }
 
@@ -376,10 +416,10 @@ static int one_step(klb_t* h) {
     const int src = h->cur, dst = 1 - h->cur;
     if (h->p.precision == KLB_FP64)
         e = launch_step<double>(h->map[src], h->cd, h->g, (double*)h->buf[dst], parts, h->err_dev, h->spin_limit,
-                                h->stream);
+                                h->inject, h->stream);
     else
         e = launch_step<float>(h->map[src], h->cf, h->g, (float*)h->buf[dst], parts, h->err_dev, h->spin_limit,
-                               h->stream);
+                               h->inject, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "step kernel");
     h->launches += 1;
     if (parts) {
@@ -466,9 +506,10 @@ int64_t klb_step_count(const klb_t* h) { return h ? h->steps : -1; }
 
 int64_t klb_launch_count(const klb_t* h) { return h ? h->launches : -1; }
 
-int klb_debug_set_spin_limit(klb_t* h, int64_t polls) {
-    if (!h || polls < 1) return KLB_E_INVAL;
-    h->spin_limit = polls;
+int klb_debug_inject_wait_timeout(klb_t* h, int64_t polls) {
+    if (!h || polls < 0) return KLB_E_INVAL;
+    h->inject = polls > 0 ? 1 : 0;
+    h->spin_limit = polls > 0 ? polls : kDefaultSpin;
     return KLB_OK;
 }
 

@@ -1,12 +1,14 @@
 // klb_device.cuh -- device-side building blocks of the FDLB step for sm_103a:
-// the velocity set, moments, F_k(T), the truncated equilibrium, the WENO5 face
-// flux, and the TMA / mbarrier primitives used by the fused step kernel.
+// the velocity set, the two arithmetic paths (FP32 production, FP64 parity),
+// ghost images, diagnostics partials, and the TMA / mbarrier primitives.
 //
 // Method: Gan, Xu, Zhang & Li, arXiv:1010.4124, Secs. II-III.
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <type_traits>
 
 namespace fdlb {
 
@@ -33,15 +35,20 @@ __host__ __device__ constexpr int sgn_y(int q) {
 }
 
 // Per-instance constants of the step, computed on the host in double and
-// converted to the arithmetic type T.
+// converted to the arithmetic type T.  Both arithmetic paths read from it.
 template <typename T>
 struct StepConst {
     T vx[NQ], vy[NQ];  // velocity components (Eq. 5)
     T v2[NQ];          // |v_q|^2
+    // FP32 path
     T cx[NQ], cy[NQ];  // dt * v_qx / dx, dt * v_qy / dy
     T ex[NQ], ey[NQ];  // WENO epsilon of the unscaled plane: eps / v_qx^2, eps / v_qy^2
     T fk[3][3];        // F_k(T) = T (fk[k][0] + T (fk[k][1] + T fk[k][2])), k = 1..3
-    T relax;           // dt / tau
+    T ginv[4][4];      // inverse Gram matrix of the collision invariants (1, v_x, v_y, |v|^2)
+    // FP64 path (the paper's formulas term by term)
+    T a4[3], pk[3], den[3];  // 4 (a_{k+1} + a_{k+2}), a_{k+1} a_{k+2}, 3 a_k (a_k - a_{k+1})(a_k - a_{k+2})
+    T dt, dx, dy, eps;
+    T relax;  // dt / tau
 };
 
 struct Geom {
@@ -51,104 +58,198 @@ struct Geom {
     int bcx_lo, bcx_hi, bcy_lo, bcy_hi;  // 0 periodic, 1 outflow, 2 fixed
 };
 
-// ---------------------------------------------------------------------------
-// Global coefficients, Eqs. (44)-(46): F_k = T (p_k - 4 s_k T + 24 T^2) / den_k
-// with the cyclic ring index; F_0 = 1 - 6 (F_1 + F_2 + F_3).
-// ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ void global_coeffs(const StepConst<T>& c, T Tm, T F[4]) {
-#pragma unroll
-    for (int k = 0; k < 3; ++k) F[k + 1] = Tm * (c.fk[k][0] + Tm * (c.fk[k][1] + Tm * c.fk[k][2]));
-    F[0] = T(1) - T(6) * (F[1] + F[2] + F[3]);
-}
-
 // Macroscopic state of one node and the equilibrium factors derived from it.
 template <typename T>
 struct NodeEq {
     T rho, ux, uy, Tm;
-    T A;        // 1 - u^2 / (2T)
-    T a, b;     // u_x / T, u_y / T
-    T rF[4];    // rho F_k
+    T A;      // 1 - u^2 / (2T)
+    T a, b;   // u_x / T, u_y / T (FP32 path)
+    T rF[4];  // rho F_k
 };
 
-// Eq. (10): rho = sum f, rho u = sum f v, rho T = sum f (v-u)^2/2, written as
-// E = sum f |v|^2 / 2 and T = E / rho - |u|^2 / 2.
-template <typename T>
-__device__ __forceinline__ NodeEq<T> node_state(const StepConst<T>& c, const T f[NQ]) {
-    T r = 0, jx = 0, jy = 0, e = 0;
+// ===========================================================================
+// FP32 production arithmetic.
+// ===========================================================================
+struct ArithF32 {
+    using T = float;
+
+    // Eqs. (44)-(46): F_k = T (p_k - 4 s_k T + 24 T^2) / den_k by Horner,
+    // F_0 = 1 - 6 (F_1 + F_2 + F_3).
+    __device__ __forceinline__ static void global_coeffs(const StepConst<T>& c, T Tm, T F[4]) {
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-        r += f[q];
-        jx += f[q] * c.vx[q];
-        jy += f[q] * c.vy[q];
-        e += f[q] * c.v2[q];
+        for (int k = 0; k < 3; ++k) F[k + 1] = Tm * (c.fk[k][0] + Tm * (c.fk[k][1] + Tm * c.fk[k][2]));
+        F[0] = 1.f - 6.f * (F[1] + F[2] + F[3]);
     }
-    NodeEq<T> s;
-    T ir = T(1) / r;
-    s.rho = r;
-    s.ux = jx * ir;
-    s.uy = jy * ir;
-    T u2 = s.ux * s.ux + s.uy * s.uy;
-    s.Tm = T(0.5) * e * ir - T(0.5) * u2;
-    T iT = T(1) / s.Tm;
-    s.A = T(1) - T(0.5) * u2 * iT;
-    s.a = s.ux * iT;
-    s.b = s.uy * iT;
-    T F[4];
-    global_coeffs(c, s.Tm, F);
+    // Eq. (10) with E = sum f |v|^2 / 2 and T = E / rho - |u|^2 / 2.
+    __device__ __forceinline__ static NodeEq<T> node_state(const StepConst<T>& c, const T f[NQ]) {
+        T r = 0, jx = 0, jy = 0, e = 0;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) s.rF[k] = r * F[k];
-    return s;
-}
+        for (int q = 0; q < NQ; ++q) {
+            r += f[q];
+            jx += f[q] * c.vx[q];
+            jy += f[q] * c.vy[q];
+            e += f[q] * c.v2[q];
+        }
+        const T ir = 1.f / r;
+        const T ux = jx * ir, uy = jy * ir;
+        return from_moments(c, r, ux, uy, 0.5f * e * ir - 0.5f * (ux * ux + uy * uy));
+    }
+    __device__ __forceinline__ static NodeEq<T> from_moments(const StepConst<T>& c, T r, T ux, T uy, T Tm) {
+        NodeEq<T> s;
+        s.rho = r;
+        s.ux = ux;
+        s.uy = uy;
+        s.Tm = Tm;
+        const T u2 = ux * ux + uy * uy;
+        const T iT = 1.f / Tm;
+        s.A = 1.f - 0.5f * u2 * iT;
+        s.a = ux * iT;
+        s.b = uy * iT;
+        T F[4];
+        global_coeffs(c, Tm, F);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) s.rF[k] = r * F[k];
+        return s;
+    }
+    // Eq. (28): f^(0) = rho F_k [A + A w + w^2/2 + w^3/6], w = v.u/T.
+    __device__ __forceinline__ static T feq(const StepConst<T>& c, const NodeEq<T>& s, int q) {
+        const T w = c.vx[q] * s.a + c.vy[q] * s.b;
+        const T br = s.A + s.A * w + w * w * (0.5f + w * (1.f / 6.f));
+        return s.rF[ring_of(q)] * br;
+    }
+    // WENO5 flux on the unscaled plane (eps already divided by v^2), over a
+    // common denominator: h = c + sum delta_q g_q P_q / sum delta_q P_q with
+    // g_q = h_q - c (Eqs. 49-51) and P_q the product of the other two
+    // (eps + sigma)^2 (Eqs. 52-55); one division instead of four.  Since
+    // every term scales with v except the absolute epsilon,
+    // h(v f; eps) = v h(f; eps / v^2): the factor v sits in the update.
+    __device__ __forceinline__ static T weno(T a, T b, T c, T d, T e, T eps) {
+        const T k13 = 13.f / 12.f;
+        const T t1 = a - 2.f * b + c, r1 = a - 4.f * b + 3.f * c;
+        const T t2 = b - 2.f * c + d, r2 = b - d;
+        const T t3 = c - 2.f * d + e, r3 = 3.f * c - 4.f * d + e;
+        const T s1 = eps + k13 * t1 * t1 + 0.25f * r1 * r1;
+        const T s2 = eps + k13 * t2 * t2 + 0.25f * r2 * r2;
+        const T s3 = eps + k13 * t3 * t3 + 0.25f * r3 * r3;
+        const T p1 = s1 * s1, p2 = s2 * s2, p3 = s3 * s3;
+        const T p23 = p2 * p3, p13 = p1 * p3, p12 = p1 * p2;
+        const T g1 = (2.f * a - 7.f * b + 5.f * c) * (1.f / 6.f);
+        const T g2 = (2.f * d - b - c) * (1.f / 6.f);
+        const T g3 = (5.f * d - 4.f * c - e) * (1.f / 6.f);
+        const T num = 0.1f * g1 * p23 + 0.6f * g2 * p13 + 0.3f * g3 * p12;
+        const T den = 0.1f * p23 + 0.6f * p13 + 0.3f * p12;
+        return c + __fdividef(num, den);
+    }
+    // BGK relaxation of all 19 planes in place: f_q <- f_q - (dt/tau) d_q with
+    // d = f - f^(0).  In exact arithmetic d carries no mass, momentum or
+    // energy (Eqs. 10-12); in FP32 the rounding of f^(0) leaves a small,
+    // state-dependent residual that would accumulate step after step, so the
+    // residual is projected out: d' = d - B^T (B B^T)^{-1} B d with
+    // B = (1, v_x, v_y, |v|^2).  The projection changes nothing in exact
+    // arithmetic and keeps the collision conservative to the rounding of d.
+    __device__ __forceinline__ static void collide(const StepConst<T>& c, const NodeEq<T>& s, T f[NQ]) {
+        T d[NQ];
+        T m0 = 0, mx = 0, my = 0, me = 0;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            d[q] = f[q] - feq(c, s, q);
+            m0 += d[q];
+            mx += d[q] * c.vx[q];
+            my += d[q] * c.vy[q];
+            me += d[q] * c.v2[q];
+        }
+        T lam[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+            lam[a] = c.ginv[a][0] * m0 + c.ginv[a][1] * mx + c.ginv[a][2] * my + c.ginv[a][3] * me;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const T dq = d[q] - (lam[0] + lam[1] * c.vx[q] + lam[2] * c.vy[q] + lam[3] * c.v2[q]);
+            f[q] = f[q] - c.relax * dq;
+        }
+    }
+};
 
-// Truncated equilibrium, Eq. (28):
-//   f_q^(0) = rho F_k [A + A w + w^2/2 + w^3/6],  w = v_q . u / T.
+// ===========================================================================
+// FP64 parity arithmetic: the paper's formulas evaluated term by term in the
+// order in which they are written (moments Eq. 10 with T from the centred
+// second moment, F_k Eqs. 44-46, f^(0) Eq. 28, the WENO5 flux of F = v f with
+// four divisions Eqs. 48-55, the update Eq. 47).  The translation units that
+// instantiate it are compiled with -fmad=false, so every operation is one
+// IEEE-rounded step; a plain CPU evaluation of the same formulas in the same
+// order therefore agrees to the last bit or close to it.
+// ===========================================================================
+struct ArithF64 {
+    using T = double;
+
+    __device__ __forceinline__ static void global_coeffs(const StepConst<T>& c, T Tm, T F[4]) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const T num = 24.0 * Tm * Tm * Tm - c.a4[k] * Tm * Tm + c.pk[k] * Tm;
+            F[k + 1] = num / c.den[k];
+        }
+        F[0] = 1.0 - 6.0 * (F[1] + F[2] + F[3]);
+    }
+    __device__ __forceinline__ static NodeEq<T> node_state(const StepConst<T>& c, const T f[NQ]) {
+        T r = 0.0, jx = 0.0, jy = 0.0;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            r += f[q];
+            jx += f[q] * c.vx[q];
+            jy += f[q] * c.vy[q];
+        }
+        const T u = jx / r, w = jy / r;
+        T e = 0.0;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const T cx = c.vx[q] - u, cy = c.vy[q] - w;
+            e += f[q] * (cx * cx + cy * cy) / 2.0;
+        }
+        return from_moments(c, r, u, w, e / r);
+    }
+    __device__ __forceinline__ static NodeEq<T> from_moments(const StepConst<T>& c, T r, T ux, T uy, T Tm) {
+        NodeEq<T> s;
+        s.rho = r;
+        s.ux = ux;
+        s.uy = uy;
+        s.Tm = Tm;
+        const T u2 = ux * ux + uy * uy;
+        s.A = 1.0 - u2 / (2.0 * Tm);
+        s.a = 0.0;
+        s.b = 0.0;
+        T F[4];
+        global_coeffs(c, Tm, F);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) s.rF[k] = r * F[k];
+        return s;
+    }
+    __device__ __forceinline__ static T feq(const StepConst<T>& c, const NodeEq<T>& s, int q) {
+        const T Tm = s.Tm, A = s.A;
+        const T vu = c.vx[q] * s.ux + c.vy[q] * s.uy;
+        const T bracket = A + (vu / Tm) * A + (vu * vu) / (2.0 * Tm * Tm) + (vu * vu * vu) / (6.0 * Tm * Tm * Tm);
+        return s.rF[ring_of(q)] * bracket;
+    }
+    // WENO5 flux of the already scaled stencil F = v f (Eqs. 48-55).
+    __device__ __forceinline__ static T weno(T a, T b, T c, T d, T e, T eps) {
+        const T h1 = (1.0 / 3.0) * a - (7.0 / 6.0) * b + (11.0 / 6.0) * c;
+        const T h2 = -(1.0 / 6.0) * b + (5.0 / 6.0) * c + (1.0 / 3.0) * d;
+        const T h3 = (1.0 / 3.0) * c + (5.0 / 6.0) * d - (1.0 / 6.0) * e;
+        const T t1 = a - 2.0 * b + c, r1 = a - 4.0 * b + 3.0 * c;
+        const T t2 = b - 2.0 * c + d, r2 = b - d;
+        const T t3 = c - 2.0 * d + e, r3 = 3.0 * c - 4.0 * d + e;
+        const T s1 = (13.0 / 12.0) * t1 * t1 + 0.25 * r1 * r1;
+        const T s2 = (13.0 / 12.0) * t2 * t2 + 0.25 * r2 * r2;
+        const T s3 = (13.0 / 12.0) * t3 * t3 + 0.25 * r3 * r3;
+        const T w1 = 0.1 / ((eps + s1) * (eps + s1));
+        const T w2 = 0.6 / ((eps + s2) * (eps + s2));
+        const T w3 = 0.3 / ((eps + s3) * (eps + s3));
+        const T ws = w1 + w2 + w3;
+        return (w1 / ws) * h1 + (w2 / ws) * h2 + (w3 / ws) * h3;
+    }
+};
+
 template <typename T>
-__device__ __forceinline__ T feq_q(const StepConst<T>& c, const NodeEq<T>& s, int q) {
-    T w = c.vx[q] * s.a + c.vy[q] * s.b;
-    T br = s.A + s.A * w + w * w * (T(0.5) + w * T(1.0 / 6.0));
-    return s.rF[ring_of(q)] * br;
-}
-
-// ---------------------------------------------------------------------------
-// Fifth-order WENO flux at I+1/2 (Eqs. 48-55) for one plane of f, with the
-// five stencil values already in upwind order (a..e = f_{I-2..I+2} for a
-// non-negative component, f_{I+3..I-1} for a negative one).  The paper applies
-// the scheme to F = v f; since every term scales with v except the absolute
-// epsilon, h(v f; eps) = v h(f; eps / v^2): the caller passes eps / v^2 and
-// multiplies by v in the update coefficient.
-//
-// The convex combination is evaluated over a common denominator,
-//   h = c + sum_q delta_q g_q P_q / sum_q delta_q P_q,
-// with g_q = h_q - c and P_q the product of the other two (eps + sigma)^2
-// terms; this is algebraically identical to Eq. (48) with Eq. (52) and needs
-// one division instead of four.
-// ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ T divide(T n, T d) { return n / d; }
-template <>
-__device__ __forceinline__ float divide<float>(float n, float d) { return __fdividef(n, d); }
-
-template <typename T>
-__device__ __forceinline__ T weno5(T a, T b, T c, T d, T e, T eps) {
-    const T k13 = T(13.0 / 12.0);
-    T t1 = a - T(2) * b + c, r1 = a - T(4) * b + T(3) * c;
-    T t2 = b - T(2) * c + d, r2 = b - d;
-    T t3 = c - T(2) * d + e, r3 = T(3) * c - T(4) * d + e;
-    T s1 = eps + k13 * t1 * t1 + T(0.25) * r1 * r1;
-    T s2 = eps + k13 * t2 * t2 + T(0.25) * r2 * r2;
-    T s3 = eps + k13 * t3 * t3 + T(0.25) * r3 * r3;
-    T p1 = s1 * s1, p2 = s2 * s2, p3 = s3 * s3;
-    T p23 = p2 * p3, p13 = p1 * p3, p12 = p1 * p2;
-    // g_q = h_q - c with h_q from Eqs. (49)-(51)
-    T g1 = (T(2) * a - T(7) * b + T(5) * c) * T(1.0 / 6.0);
-    T g2 = (T(2) * d - b - c) * T(1.0 / 6.0);
-    T g3 = (T(5) * d - T(4) * c - e) * T(1.0 / 6.0);
-    T num = T(0.1) * g1 * p23 + T(0.6) * g2 * p13 + T(0.3) * g3 * p12;
-    T den = T(0.1) * p23 + T(0.6) * p13 + T(0.3) * p12;
-    return c + divide(num, den);
-}
-
+using Arith = typename std::conditional<std::is_same<T, float>::value, ArithF32, ArithF64>::type;
 
 // ---------------------------------------------------------------------------
 // Ghost images.  A node next to a periodic side is also written to the ghost

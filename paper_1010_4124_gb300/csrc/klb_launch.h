@@ -13,11 +13,13 @@ constexpr long long kDrainPolls = 1ll << 22;
 // Default poll budget of the tile-load wait.
 constexpr long long kDefaultSpin = 1ll << 22;
 
+// One fused step from the state behind `in_map` into `out` (klb_step_f32.cu /
+// klb_step_f64.cu).  diag_partials != NULL also reduces the diagnostics of the
+// input state; spin_limit bounds the tile-load wait; inject != 0 adds a wait
+// on a barrier nothing arrives on (fault injection for tests).
 template <typename T>
 cudaError_t launch_step(const CUtensorMap& in_map, const StepConst<T>& c, const Geom& g, T* out,
-                        double* diag_partials, int* err, long long spin_limit, cudaStream_t stream);
-template <typename T>
-size_t step_smem_bytes();
+                        double* diag_partials, int* err, long long spin_limit, int inject, cudaStream_t stream);
 void step_tile_shape(int precision, int* tx, int* ty);
 
 // f := f^(0)(fields) on the interior, with ghost images (klb_aux.cu).

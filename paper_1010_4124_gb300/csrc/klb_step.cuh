@@ -1,4 +1,5 @@
-// klb_step.cu -- the fused FDLB time step for sm_103a.
+// klb_step.cuh -- the fused FDLB time step for sm_103a (kernel template;
+// klb_step_f32.cu and klb_step_f64.cu instantiate it).
 //
 // One launch = one forward-Euler step (Eq. 47 of arXiv:1010.4124) over the
 // whole grid.  Each CTA owns a TX x TY tile of interior nodes:
@@ -18,6 +19,7 @@
 //      in the output buffer, so the next launch finds its ghosts filled;
 //   5. optionally, the CTA reduces the diagnostics of its input nodes in FP64
 //      to one partial record (finished by klb_diag_finalize).
+#pragma once
 #include "klb_device.cuh"
 #include "klb_launch.h"
 
@@ -45,54 +47,75 @@ struct SmemLayout {
     static constexpr size_t BYTES = TILE_BYTES + sizeof(T) * (HX + HY);
 };
 
-// WENO5 x-face between smem columns sx-1 and sx of row sy, plane P.
+// WENO5 x-face between smem columns sx-1 and sx of row sy, plane P, for the
+// velocity component v of sign SGN.  The FP32 path reconstructs the unscaled
+// plane (eps / v^2, factor v in the update); the FP64 path reconstructs
+// F = v f exactly as Eq. (48) states it.
 template <typename T, int SX, int SGN>
-__device__ __forceinline__ T face_x(const T* __restrict__ P, int sy, int sx, T eps) {
+__device__ __forceinline__ T face_x(const T* P, int sy, int sx, T v, T eps) {
     const T* r = P + sy * SX;
-    if (SGN > 0) return weno5<T>(r[sx - 3], r[sx - 2], r[sx - 1], r[sx], r[sx + 1], eps);
-    return weno5<T>(r[sx + 2], r[sx + 1], r[sx], r[sx - 1], r[sx - 2], eps);
+    const T s = std::is_same<T, float>::value ? T(1) : v;
+    if (SGN > 0)
+        return Arith<T>::weno(s * r[sx - 3], s * r[sx - 2], s * r[sx - 1], s * r[sx], s * r[sx + 1], eps);
+    return Arith<T>::weno(s * r[sx + 2], s * r[sx + 1], s * r[sx], s * r[sx - 1], s * r[sx - 2], eps);
 }
 // WENO5 y-face between smem rows sy-1 and sy of column sx, plane P.
 template <typename T, int SX, int SGN>
-__device__ __forceinline__ T face_y(const T* __restrict__ P, int sy, int sx, T eps) {
+__device__ __forceinline__ T face_y(const T* P, int sy, int sx, T v, T eps) {
     const T* c = P + sx;
+    const T s = std::is_same<T, float>::value ? T(1) : v;
     if (SGN > 0)
-        return weno5<T>(c[(sy - 3) * SX], c[(sy - 2) * SX], c[(sy - 1) * SX], c[sy * SX], c[(sy + 1) * SX], eps);
-    return weno5<T>(c[(sy + 2) * SX], c[(sy + 1) * SX], c[sy * SX], c[(sy - 1) * SX], c[(sy - 2) * SX], eps);
+        return Arith<T>::weno(s * c[(sy - 3) * SX], s * c[(sy - 2) * SX], s * c[(sy - 1) * SX], s * c[sy * SX],
+                              s * c[(sy + 1) * SX], eps);
+    return Arith<T>::weno(s * c[(sy + 2) * SX], s * c[(sy + 1) * SX], s * c[sy * SX], s * c[(sy - 1) * SX],
+                          s * c[(sy - 2) * SX], eps);
 }
 
+// The shared-memory face buffers carry values between threads across
+// __syncthreads(), so they must not be declared __restrict__: that would let
+// the compiler reuse a neighbour's face loaded for the previous velocity.
 template <typename T, int TX, int TY, int Q>
-__device__ __forceinline__ void velocity_update(const StepConst<T>& c, const Geom& g, const T* __restrict__ tile,
-                                                T* __restrict__ hx, T* __restrict__ hy, const NodeEq<T>& s,
+__device__ __forceinline__ void velocity_update(const StepConst<T>& c, const Geom& g, const T* tile,
+                                                T* hx, T* hy, const NodeEq<T>& s,
                                                 T fq, int tx, int ty, int ix, int iy, bool active,
                                                 T* __restrict__ out) {
     using L = SmemLayout<T, TX, TY>;
     constexpr int SX = L::SX;
     constexpr int SGX = sgn_x(Q), SGY = sgn_y(Q);
+    constexpr bool F32 = std::is_same<T, float>::value;
     const T* P = tile + Q * L::PLANE;
     const int sx = tx + 4, sy = ty + 3;
     const int tid = threadIdx.x;
+    const T epsx = F32 ? c.ex[Q] : c.eps, epsy = F32 ? c.ey[Q] : c.eps;
     T hl = 0, hb = 0;
     if (SGX != 0) {
-        hl = face_x<T, SX, SGX>(P, sy, sx, c.ex[Q]);
+        hl = face_x<T, SX, SGX>(P, sy, sx, c.vx[Q], epsx);
         hx[ty * (TX + 1) + tx] = hl;
     }
     if (SGY != 0) {
-        hb = face_y<T, SX, SGY>(P, sy, sx, c.ey[Q]);
+        hb = face_y<T, SX, SGY>(P, sy, sx, c.vy[Q], epsy);
         hy[ty * TX + tx] = hb;
     }
     // tile edge faces: warp 0 the top row of y faces, warp 1 the right column of x faces
-    if (SGY != 0 && tid < TX) hy[TY * TX + tid] = face_y<T, SX, SGY>(P, TY + 3, tid + 4, c.ey[Q]);
+    if (SGY != 0 && tid < TX) hy[TY * TX + tid] = face_y<T, SX, SGY>(P, TY + 3, tid + 4, c.vy[Q], epsy);
     if (SGX != 0 && tid >= 32 && tid < 32 + TY) {
         int r = tid - 32;
-        hx[r * (TX + 1) + TX] = face_x<T, SX, SGX>(P, r + 3, TX + 4, c.ex[Q]);
+        hx[r * (TX + 1) + TX] = face_x<T, SX, SGX>(P, r + 3, TX + 4, c.vx[Q], epsx);
     }
     __syncthreads();
-    T div = 0;
-    if (SGX != 0) div += c.cx[Q] * (hx[ty * (TX + 1) + tx + 1] - hl);
-    if (SGY != 0) div += c.cy[Q] * (hy[(ty + 1) * TX + tx] - hb);
-    T fe = feq_q(c, s, Q);
-    T fn = fq - div - c.relax * (fq - fe);
+    T fn;
+    if constexpr (F32) {
+        // fq is the post-collision value; subtract the flux divergence
+        T div = 0;
+        if (SGX != 0) div += c.cx[Q] * (hx[ty * (TX + 1) + tx + 1] - hl);
+        if (SGY != 0) div += c.cy[Q] * (hy[(ty + 1) * TX + tx] - hb);
+        fn = fq - div;
+    } else {
+        // Eq. (47) as written: f - dt (dh_x/dx + dh_y/dy) - (dt/tau)(f - f^(0))
+        const T dhx = SGX != 0 ? hx[ty * (TX + 1) + tx + 1] - hl : T(0);
+        const T dhy = SGY != 0 ? hy[(ty + 1) * TX + tx] - hb : T(0);
+        fn = fq - c.dt * (dhx / c.dx + dhy / c.dy) - c.relax * (fq - Arith<T>::feq(c, s, Q));
+    }
     if (active) store_with_images(out, g, Q, ix, iy, fn);
     __syncthreads();
 }
@@ -116,18 +139,20 @@ template <typename T, int TX, int TY>
 __global__ void __launch_bounds__(TX* TY) step_kernel(const __grid_constant__ CUtensorMap in_map,
                                                       const __grid_constant__ StepConst<T> c, const Geom g,
                                                       T* __restrict__ out, double* __restrict__ diag_partials,
-                                                      int* __restrict__ err, long long spin_limit) {
+                                                      int* __restrict__ err, long long spin_limit, int inject) {
     using L = SmemLayout<T, TX, TY>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     T* tile = reinterpret_cast<T*>(smem_raw);
     T* hx = reinterpret_cast<T*>(smem_raw + L::TILE_BYTES);
     T* hy = hx + L::HX;
     __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(8) uint64_t never;  // fault injection: a barrier nothing arrives on
 
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const uint32_t b = smem_u32(&bar);
     if (threadIdx.x == 0) {
         mbar_init(b, 1);
+        mbar_init(smem_u32(&never), 1);
         fence_barrier_init();
         fence_proxy_async();
         mbar_arrive_expect_tx(b, (uint32_t)L::TILE_BYTES);
@@ -136,7 +161,8 @@ __global__ void __launch_bounds__(TX* TY) step_kernel(const __grid_constant__ CU
     }
     __syncthreads();
     // the verdict of the bounded wait is made uniform across the CTA
-    const bool late = !mbar_wait_bounded(b, 0, spin_limit);
+    bool late = !mbar_wait_bounded(b, 0, spin_limit);
+    if (inject) late = late || !mbar_wait_bounded(smem_u32(&never), 0, spin_limit);
     if (__syncthreads_or(late)) {
         if (threadIdx.x == 0) atomicOr(err, ERR_TIMEOUT);
         // let the copy in flight land before the CTA releases its shared memory
@@ -152,7 +178,7 @@ __global__ void __launch_bounds__(TX* TY) step_kernel(const __grid_constant__ CU
     T f[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) f[q] = tile[q * L::PLANE + sy * L::SX + sx];
-    NodeEq<T> s = node_state(c, f);
+    NodeEq<T> s = Arith<T>::node_state(c, f);
 
     if (diag_partials != nullptr) {
         double v[8];
@@ -160,18 +186,14 @@ __global__ void __launch_bounds__(TX* TY) step_kernel(const __grid_constant__ CU
         diag_block_reduce<TX * TY>(v, diag_partials + 8ll * (blockIdx.y * gridDim.x + blockIdx.x));
     }
 
+    if constexpr (std::is_same<T, float>::value) Arith<T>::collide(c, s, f);  // f <- post-collision values
     VelLoop<T, TX, TY, 0>::run(c, g, tile, hx, hy, s, f, tx, ty, ix, iy, active, out);
 }
 
 template <typename T>
-size_t step_smem_bytes() {
-    using TT = StepTile<T>;
-    return SmemLayout<T, TT::TX, TT::TY>::BYTES;
-}
-
-template <typename T>
-cudaError_t launch_step(const CUtensorMap& in_map, const StepConst<T>& c, const Geom& g, T* out,
-                        double* diag_partials, int* err, long long spin_limit, cudaStream_t stream) {
+cudaError_t launch_step_impl(const CUtensorMap& in_map, const StepConst<T>& c, const Geom& g, T* out,
+                             double* diag_partials, int* err, long long spin_limit, int inject,
+                             cudaStream_t stream) {
     using TT = StepTile<T>;
     constexpr int TX = TT::TX, TY = TT::TY;
     const size_t smem = SmemLayout<T, TX, TY>::BYTES;
@@ -183,23 +205,9 @@ cudaError_t launch_step(const CUtensorMap& in_map, const StepConst<T>& c, const 
         attr_set = true;
     }
     dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY);
-    step_kernel<T, TX, TY><<<grid, TX * TY, smem, stream>>>(in_map, c, g, out, diag_partials, err, spin_limit);
+    step_kernel<T, TX, TY><<<grid, TX * TY, smem, stream>>>(in_map, c, g, out, diag_partials, err, spin_limit,
+                                                            inject);
     return cudaGetLastError();
 }
-
-void step_tile_shape(int precision, int* tx, int* ty) {
-    if (precision == 1) {
-        *tx = StepTile<double>::TX;
-        *ty = StepTile<double>::TY;
-    } else {
-        *tx = StepTile<float>::TX;
-        *ty = StepTile<float>::TY;
-    }
-}
-
-template cudaError_t launch_step<float>(const CUtensorMap&, const StepConst<float>&, const Geom&, float*, double*,
-                                        int*, long long, cudaStream_t);
-template cudaError_t launch_step<double>(const CUtensorMap&, const StepConst<double>&, const Geom&, double*,
-                                         double*, int*, long long, cudaStream_t);
 
 }  // namespace fdlb

@@ -72,7 +72,7 @@ def lib():
             "klb_layout": (C.c_int, [vp, C.POINTER(vp), C.POINTER(i64), C.POINTER(i64), C.POINTER(i32),
                                      C.POINTER(i32)]),
             "klb_launch_count": (i64, [vp]),
-            "klb_debug_set_spin_limit": (C.c_int, [vp, i64]),
+            "klb_debug_inject_wait_timeout": (C.c_int, [vp, i64]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -214,5 +214,5 @@ class Klb:
                                         C.byref(gy)))
         return base.value, pitch.value, plane.value, gx.value, gy.value
 
-    def debug_set_spin_limit(self, polls: int):
-        _check(self.h, lib().klb_debug_set_spin_limit(self.h, int(polls)))
+    def debug_inject_wait_timeout(self, polls: int):
+        _check(self.h, lib().klb_debug_inject_wait_timeout(self.h, int(polls)))
