@@ -35,6 +35,13 @@ def rel_err_fields(a_f, b_f, p: core.Params):
     }
 
 
+def rel_err_global(a_f, b_f):
+    """||a - b||_inf over all planes / ||b||_inf over all planes (the scale of f):
+    the FP32 measure, since planes whose F_k(T) is near a root carry values far
+    below the others and an FP32 rounding of a large term lands on them."""
+    return float(np.abs(a_f - b_f).max() / np.abs(b_f).max())
+
+
 def rel_err_planes(a_f, b_f):
     """max over the 19 planes of ||a_q - b_q||_inf / ||b_q||_inf."""
     worst = 0.0
