@@ -155,6 +155,16 @@ int klb_layout(const klb_t* h, const void** base, int64_t* pitch, int64_t* plane
  * library launched on its stream). */
 int64_t klb_launch_count(const klb_t* h);
 
+/* Kernel variant (tile shape) of the FP32 step: 0 = tiles of 31 x 16 nodes,
+ * one CTA of 16 warps per SM; 1 = tiles of 31 x 8 nodes, two CTAs of 8 warps
+ * per SM.  Every node is computed by the same arithmetic in both, so the
+ * states are bitwise identical; only the speed differs (the diagnostics sums
+ * may differ in the last bits, being reduced in another order).  The FP64
+ * step has variant 0 only.  Synchronises the handle's stream.  Errors:
+ * KLB_E_INVAL. */
+int klb_set_variant(klb_t* h, int variant);
+int klb_get_variant(const klb_t* h);
+
 /* Fault injection for tests.  With polls > 0, every later step launch also
  * waits, with a budget of `polls` polls, on a device barrier that nothing
  * arrives on (a flag that nothing sets): the wait runs out, each CTA records

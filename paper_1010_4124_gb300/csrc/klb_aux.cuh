@@ -171,7 +171,7 @@ cudaError_t launch_diag_partials_tiles(const StepConst<T>& c, const Geom& g, con
     return cudaGetLastError();
 }
 
-#define KLB_AUX_INST(T, TX, TY)                                                                                  \
+#define KLB_AUX_INST(T)                                                                                  \
     template cudaError_t launch_init_feq<T>(const StepConst<T>&, const Geom&, const double*, const double*,     \
                                             const double*, const double*, T*, T*, cudaStream_t);              \
     template cudaError_t launch_fixed_ghosts<T>(const StepConst<T>&, const Geom&, const double*, const double*, \
@@ -179,11 +179,6 @@ cudaError_t launch_diag_partials_tiles(const StepConst<T>& c, const Geom& g, con
     template cudaError_t launch_set_f<T>(const Geom&, const double*, T*, cudaStream_t);                         \
     template cudaError_t launch_get_f<T>(const Geom&, const T*, double*, cudaStream_t);                         \
     template cudaError_t launch_fields<T>(const StepConst<T>&, const Geom&, const T*, double*, double*, double*, \
-                                          double*, cudaStream_t);                                              \
-    template <>                                                                                                  \
-    cudaError_t launch_diag_partials<T>(const StepConst<T>& c, const Geom& g, const T* f, double* partials,     \
-                                        cudaStream_t s) {                                                      \
-        return launch_diag_partials_tiles<T, TX, TY>(c, g, f, partials, s);                                    \
-    }
+                                          double*, cudaStream_t);
 
 }  // namespace fdlb

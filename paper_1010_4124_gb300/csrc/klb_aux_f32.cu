@@ -4,7 +4,7 @@
 
 namespace fdlb {
 
-KLB_AUX_INST(float, 32, 16)
+KLB_AUX_INST(float)
 
 // One block folds all partial records, in record order per thread and a fixed
 // tree across threads.

@@ -38,6 +38,7 @@ struct klb {
     int64_t launches = 0;
     long long spin_limit = kDefaultSpin;
     int inject = 0;
+    int variant = 0;  // FP32 tile shape (see klb_set_variant)
     std::string err;
 };
 
@@ -78,8 +79,9 @@ static void fill_const(const klb_params& p, StepConst<T>& c) {
         c.v2[q] = T(vx * vx + vy * vy);
         c.cx[q] = T(p.dt * vx / p.dx);
         c.cy[q] = T(p.dt * vy / p.dy);
-        c.ex[q] = vx != 0 ? T(eps / (vx * vx)) : T(0);
-        c.ey[q] = vy != 0 ? T(eps / (vy * vy)) : T(0);
+        // FP32 weno() works with 3 sigma, hence 3 eps; the FP64 path uses eps itself
+        c.ex[q] = vx != 0 ? T(3.0 * eps / (vx * vx)) : T(0);
+        c.ey[q] = vy != 0 ? T(3.0 * eps / (vy * vy)) : T(0);
     }
     // F_k(T) = T [a_{k+1} a_{k+2} - 4 (a_{k+1} + a_{k+2}) T + 24 T^2] / [3 a_k (a_k - a_{k+1})(a_k - a_{k+2})]
     for (int k = 0; k < 3; ++k) {
@@ -154,12 +156,23 @@ static EncodeTiledFn encode_fn() {
 static int make_map(klb_t* h, void* base, CUtensorMap* map) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return fail(h, KLB_E_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
-    int TX, TY;
-    step_tile_shape(h->p.precision, &TX, &TY);
     const Geom& g = h->g;
     cuuint64_t dims[3] = {(cuuint64_t)g.px, (cuuint64_t)(g.ny + 2 * GY), (cuuint64_t)NQ};
     cuuint64_t strides[2] = {(cuuint64_t)g.px * h->esize, (cuuint64_t)g.plane * h->esize};
-    cuuint32_t box[3] = {(cuuint32_t)(TX + 8), (cuuint32_t)(TY + 6), (cuuint32_t)NQ};
+    cuuint32_t box[3];
+    if (h->p.precision == KLB_FP64) {  // one tile of TX x TY nodes plus halo
+        int TX, TY;
+        f64_tile(&TX, &TY);
+        box[0] = (cuuint32_t)(TX + 8);
+        box[1] = (cuuint32_t)(TY + 6);
+        box[2] = (cuuint32_t)NQ;
+    } else {  // one tile of the persistent FP32 kernel
+        unsigned bx, by, bz;
+        f32_box(h->variant, &bx, &by, &bz);
+        box[0] = bx;
+        box[1] = by;
+        box[2] = bz;
+    }
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = fn(map, h->p.precision == KLB_FP64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
                     3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -225,9 +238,14 @@ int klb_create(const klb_params* pin, klb_t** out) {
     g.bcy_hi = p.bc_y_hi;
     fill_const(h->p, h->cf);
     fill_const(h->p, h->cd);
-    int TX, TY;
-    step_tile_shape(p.precision, &TX, &TY);
-    h->nparts = ((p.nx + TX - 1) / TX) * ((p.ny + TY - 1) / TY);
+    if (p.precision == KLB_FP64) {
+        int TX, TY;
+        f64_tile(&TX, &TY);
+        h->nparts = ((p.nx + TX - 1) / TX) * ((p.ny + TY - 1) / TY);
+    } else {
+        // room for the partial records of either tile shape
+        h->nparts = std::max(f32_grid(p.nx, p.ny, 0), f32_grid(p.nx, p.ny, 1));
+    }
     h->cap = p.diag_capacity > 0 ? p.diag_capacity : 4096;
 
     auto cleanup = [&](int code) {
@@ -408,6 +426,12 @@ int klb_get_f(klb_t* h, double* f, int on_device) {
     return klb_sync(h);
 }
 
+// partial diagnostics records written by one launch of the current kernel
+static int records(const klb_t* h) {
+    if (h->p.precision == KLB_FP64) return h->nparts;
+    return f32_grid(h->g.nx, h->g.ny, h->variant);
+}
+
 // one step: optional fused diagnostics of the input state, then ping-pong
 static int one_step(klb_t* h) {
     double* parts = nullptr;
@@ -418,12 +442,12 @@ static int one_step(klb_t* h) {
         e = launch_step<double>(h->map[src], h->cd, h->g, (double*)h->buf[dst], parts, h->err_dev, h->spin_limit,
                                 h->inject, h->stream);
     else
-        e = launch_step<float>(h->map[src], h->cf, h->g, (float*)h->buf[dst], parts, h->err_dev, h->spin_limit,
-                               h->inject, h->stream);
+        e = launch_step_f32(h->map[src], h->cf, h->g, (float*)h->buf[dst], parts, h->err_dev, h->spin_limit,
+                            h->inject, h->variant, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "step kernel");
     h->launches += 1;
     if (parts) {
-        e = launch_diag_finalize(parts, h->nparts, h->diag_ring + 7 * (h->nsamples % h->cap), h->err_dev,
+        e = launch_diag_finalize(parts, records(h), h->diag_ring + 7 * (h->nsamples % h->cap), h->err_dev,
                                  h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "diagnostics finalize");
         h->launches += 1;
@@ -453,10 +477,10 @@ static int flush_sample(klb_t* h) {
     cudaError_t e = h->p.precision == KLB_FP64
                         ? launch_diag_partials<double>(h->cd, h->g, (const double*)h->buf[h->cur],
                                                        h->diag_partials, h->stream)
-                        : launch_diag_partials<float>(h->cf, h->g, (const float*)h->buf[h->cur],
-                                                      h->diag_partials, h->stream);
+                        : launch_diag_f32(h->cf, h->g, (const float*)h->buf[h->cur], h->diag_partials,
+                                          h->variant, h->stream);
     if (e == cudaSuccess)
-        e = launch_diag_finalize(h->diag_partials, h->nparts, h->diag_ring + 7 * (h->nsamples % h->cap),
+        e = launch_diag_finalize(h->diag_partials, records(h), h->diag_ring + 7 * (h->nsamples % h->cap),
                                  h->err_dev, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "diagnostics kernels");
     h->launches += 2;
@@ -512,6 +536,29 @@ int klb_debug_inject_wait_timeout(klb_t* h, int64_t polls) {
     h->spin_limit = polls > 0 ? polls : kDefaultSpin;
     return KLB_OK;
 }
+
+int klb_set_variant(klb_t* h, int variant) {
+    if (!h) return KLB_E_INVAL;
+    if (variant < 0 || variant > 1) return fail(h, KLB_E_INVAL, "unknown kernel variant");
+    if (h->p.precision == KLB_FP64) {
+        if (variant != 0) return fail(h, KLB_E_INVAL, "the FP64 step has one variant");
+        return KLB_OK;
+    }
+    CK(h, cudaStreamSynchronize(h->stream));
+    const int old = h->variant;
+    h->variant = variant;
+    for (int i = 0; i < 2; ++i) {
+        int r = make_map(h, h->buf[i], &h->map[i]);
+        if (r != KLB_OK) {
+            h->variant = old;
+            for (int j = 0; j < 2; ++j) make_map(h, h->buf[j], &h->map[j]);
+            return r;
+        }
+    }
+    return KLB_OK;
+}
+
+int klb_get_variant(const klb_t* h) { return h ? h->variant : -1; }
 
 int klb_layout(const klb_t* h, const void** base, int64_t* pitch, int64_t* plane, int32_t* gx, int32_t* gy) {
     if (!h) return KLB_E_INVAL;

@@ -42,7 +42,7 @@ struct StepConst {
     T v2[NQ];          // |v_q|^2
     // FP32 path
     T cx[NQ], cy[NQ];  // dt * v_qx / dx, dt * v_qy / dy
-    T ex[NQ], ey[NQ];  // WENO epsilon of the unscaled plane: eps / v_qx^2, eps / v_qy^2
+    T ex[NQ], ey[NQ];  // FP32 WENO: 3 eps / v_qx^2, 3 eps / v_qy^2 (unscaled plane, 3 sigma)
     T fk[3][3];        // F_k(T) = T (fk[k][0] + T (fk[k][1] + T fk[k][2])), k = 1..3
     T ginv[4][4];      // inverse Gram matrix of the collision invariants (1, v_x, v_y, |v|^2)
     // FP64 path (the paper's formulas term by term)
@@ -66,6 +66,14 @@ struct NodeEq {
     T a, b;   // u_x / T, u_y / T (FP32 path)
     T rF[4];  // rho F_k
 };
+
+// Hardware reciprocal approximation (one MUFU instruction, max error 1 ulp);
+// the weights it feeds are ratios of smooth positive quantities.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 
 // ===========================================================================
 // FP32 production arithmetic.
@@ -120,25 +128,63 @@ struct ArithF32 {
     // WENO5 flux on the unscaled plane (eps already divided by v^2), over a
     // common denominator: h = c + sum delta_q g_q P_q / sum delta_q P_q with
     // g_q = h_q - c (Eqs. 49-51) and P_q the product of the other two
-    // (eps + sigma)^2 (Eqs. 52-55); one division instead of four.  Since
-    // every term scales with v except the absolute epsilon,
+    // (eps + sigma)^2 (Eqs. 52-55); one reciprocal instead of four divisions.
+    // Since every term scales with v except the absolute epsilon,
     // h(v f; eps) = v h(f; eps / v^2): the factor v sits in the update.
-    __device__ __forceinline__ static T weno(T a, T b, T c, T d, T e, T eps) {
-        const T k13 = 13.f / 12.f;
-        const T t1 = a - 2.f * b + c, r1 = a - 4.f * b + 3.f * c;
-        const T t2 = b - 2.f * c + d, r2 = b - d;
-        const T t3 = c - 2.f * d + e, r3 = 3.f * c - 4.f * d + e;
-        const T s1 = eps + k13 * t1 * t1 + 0.25f * r1 * r1;
-        const T s2 = eps + k13 * t2 * t2 + 0.25f * r2 * r2;
-        const T s3 = eps + k13 * t3 * t3 + 0.25f * r3 * r3;
-        const T p1 = s1 * s1, p2 = s2 * s2, p3 = s3 * s3;
-        const T p23 = p2 * p3, p13 = p1 * p3, p12 = p1 * p2;
-        const T g1 = (2.f * a - 7.f * b + 5.f * c) * (1.f / 6.f);
-        const T g2 = (2.f * d - b - c) * (1.f / 6.f);
-        const T g3 = (5.f * d - 4.f * c - e) * (1.f / 6.f);
-        const T num = 0.1f * g1 * p23 + 0.6f * g2 * p13 + 0.3f * g3 * p12;
-        const T den = 0.1f * p23 + 0.6f * p13 + 0.3f * p12;
-        return c + __fdividef(num, den);
+    __device__ __forceinline__ static T weno(T a, T b, T c, T d, T e, T eps3) {
+        // differences of neighbouring values; in them the smoothness
+        // indicators of Eqs. (53)-(55) read
+        //   3 sigma_1 = 4 D1^2 - 11 D1 D2 + 10 D2^2,
+        //   3 sigma_2 = 4 D2^2 -  5 D2 D3 +  4 D3^2,
+        //   3 sigma_3 = 10 D3^2 - 11 D3 D4 + 4 D4^2,
+        // and the candidates of Eqs. (49)-(51) relative to c read
+        //   h_1 - c = (5 D2 - 2 D1)/6, h_2 - c = (D2 + 2 D3)/6, h_3 - c = (4 D3 - D4)/6.
+        // The weights use 3 sigma and 3 eps (eps3): the common factor cancels.
+        // With e4 = d - e = -D4 (no negation needed) and the optimal weights and
+        // the 1/6 of the candidates folded into the differences,
+        //   h = c + sum_q (delta_q / 6) G_q P_q / sum_q delta_q P_q.
+        // Every operation is an explicitly rounded multiply, add or fused
+        // multiply-add, in the same order as each lane of weno2(), so the
+        // scalar and packed evaluations give the same bits.
+        const T d1 = fmaf(a, -1.f, b), d2 = fmaf(b, -1.f, c), d3 = fmaf(c, -1.f, d), e4 = fmaf(e, -1.f, d);
+        const T a2 = __fmul_rn(d2, d2), a3 = __fmul_rn(d3, d3);
+        const T s1 = fmaf(d1, fmaf(4.f, d1, __fmul_rn(-11.f, d2)), fmaf(10.f, a2, eps3));
+        const T s2 = fmaf(4.f, __fadd_rn(a2, a3), fmaf(__fmul_rn(-5.f, d2), d3, eps3));
+        const T s3 = fmaf(e4, fmaf(4.f, e4, __fmul_rn(11.f, d3)), fmaf(10.f, a3, eps3));
+        const T p1 = __fmul_rn(s1, s1), p2 = __fmul_rn(s2, s2), p3 = __fmul_rn(s3, s3);
+        const T P23 = __fmul_rn(p2, p3), P13 = __fmul_rn(p1, p3), P12 = __fmul_rn(p1, p2);
+        const T G1 = fmaf(0.5f / 6.f, d2, __fmul_rn(-0.2f / 6.f, d1));
+        const T G2 = fmaf(1.2f / 6.f, d3, __fmul_rn(0.1f, d2));
+        const T G3 = fmaf(1.2f / 6.f, d3, __fmul_rn(0.05f, e4));
+        const T num = fmaf(G1, P23, fmaf(G2, P13, __fmul_rn(G3, P12)));
+        const T den = fmaf(0.1f, P23, fmaf(0.6f, P13, __fmul_rn(0.3f, P12)));
+        return fmaf(num, rcp_approx(den), c);
+    }
+    // The same flux for two independent faces at once (packed f32x2
+    // arithmetic: one instruction for both lanes of the pair).
+    __device__ __forceinline__ static float2 weno2(float2 a, float2 b, float2 c, float2 d, float2 e, float2 eps3) {
+        // lane by lane the same operations as weno()
+        const float2 m1 = make_float2(-1.f, -1.f);
+        const float2 d1 = __ffma2_rn(a, m1, b), d2 = __ffma2_rn(b, m1, c);
+        const float2 d3 = __ffma2_rn(c, m1, d), e4 = __ffma2_rn(e, m1, d);
+        const float2 a2 = __fmul2_rn(d2, d2), a3 = __fmul2_rn(d3, d3);
+        const float2 k4 = make_float2(4.f, 4.f), k10 = make_float2(10.f, 10.f);
+        const float2 s1 = __ffma2_rn(d1, __ffma2_rn(k4, d1, __fmul2_rn(make_float2(-11.f, -11.f), d2)),
+                                     __ffma2_rn(k10, a2, eps3));
+        const float2 s2 = __ffma2_rn(k4, __fadd2_rn(a2, a3), __ffma2_rn(__fmul2_rn(make_float2(-5.f, -5.f), d2), d3, eps3));
+        const float2 s3 = __ffma2_rn(e4, __ffma2_rn(k4, e4, __fmul2_rn(make_float2(11.f, 11.f), d3)),
+                                     __ffma2_rn(k10, a3, eps3));
+        const float2 p1 = __fmul2_rn(s1, s1), p2 = __fmul2_rn(s2, s2), p3 = __fmul2_rn(s3, s3);
+        const float2 P23 = __fmul2_rn(p2, p3), P13 = __fmul2_rn(p1, p3), P12 = __fmul2_rn(p1, p2);
+        // (delta_1/6)(5 D2 - 2 D1), (delta_2/6)(D2 + 2 D3), (delta_3/6)(4 D3 - D4)
+        const float2 G1 = __ffma2_rn(make_float2(0.5f / 6.f, 0.5f / 6.f), d2, __fmul2_rn(make_float2(-0.2f / 6.f, -0.2f / 6.f), d1));
+        const float2 G2 = __ffma2_rn(make_float2(1.2f / 6.f, 1.2f / 6.f), d3, __fmul2_rn(make_float2(0.1f, 0.1f), d2));
+        const float2 G3 = __ffma2_rn(make_float2(1.2f / 6.f, 1.2f / 6.f), d3, __fmul2_rn(make_float2(0.05f, 0.05f), e4));
+        const float2 num = __ffma2_rn(G1, P23, __ffma2_rn(G2, P13, __fmul2_rn(G3, P12)));
+        const float2 den = __ffma2_rn(make_float2(0.1f, 0.1f), P23,
+                                      __ffma2_rn(make_float2(0.6f, 0.6f), P13, __fmul2_rn(make_float2(0.3f, 0.3f), P12)));
+        const float2 r = make_float2(rcp_approx(den.x), rcp_approx(den.y));
+        return __ffma2_rn(num, r, c);
     }
     // BGK relaxation of all 19 planes in place: f_q <- f_q - (dt/tau) d_q with
     // d = f - f^(0).  In exact arithmetic d carries no mass, momentum or
@@ -259,11 +305,28 @@ using Arith = typename std::conditional<std::is_same<T, float>::value, ArithF32,
 // ghosts (Eq. 57) are written once at initialisation and never touched.
 // Corner ghosts are never read by the dimension-by-dimension stencils.
 // ---------------------------------------------------------------------------
+// true when node (ix, iy) has ghost images to write
+__device__ __forceinline__ bool has_images(const Geom& g, int ix, int iy) {
+    const bool xe = g.bcx_lo == 0 ? (ix < 3 || ix >= g.nx - 3)
+                                  : ((ix == 0 && g.bcx_lo == 1) || (ix == g.nx - 1 && g.bcx_hi == 1));
+    const bool ye = g.bcy_lo == 0 ? (iy < 3 || iy >= g.ny - 3)
+                                  : ((iy == 0 && g.bcy_lo == 1) || (iy == g.ny - 1 && g.bcy_hi == 1));
+    return xe || ye;
+}
+
+template <typename T>
+__device__ __forceinline__ void write_images(T* __restrict__ out, const Geom& g, int q, int ix, int iy, T val);
+
 template <typename T>
 __device__ __forceinline__ void store_with_images(T* __restrict__ out, const Geom& g, int q, int ix, int iy,
                                                   T val) {
+    out[(long long)q * g.plane + (long long)(iy + GY) * g.px + (ix + GX)] = val;
+    write_images(out, g, q, ix, iy, val);
+}
+
+template <typename T>
+__device__ __forceinline__ void write_images(T* __restrict__ out, const Geom& g, int q, int ix, int iy, T val) {
     const long long base = (long long)q * g.plane;
-    out[base + (long long)(iy + GY) * g.px + (ix + GX)] = val;
     // x ghost images (interior rows only)
     const bool xper = g.bcx_lo == 0;
     if (xper) {

@@ -20,7 +20,19 @@ constexpr long long kDefaultSpin = 1ll << 22;
 template <typename T>
 cudaError_t launch_step(const CUtensorMap& in_map, const StepConst<T>& c, const Geom& g, T* out,
                         double* diag_partials, int* err, long long spin_limit, int inject, cudaStream_t stream);
-void step_tile_shape(int precision, int* tx, int* ty);
+// FP64 step: TX x TY tiles, one thread per node (klb_step_f64.cu)
+void f64_tile(int* tx, int* ty);
+// FP32 step (klb_step_f32.cu): persistent CTAs over tiles of 31 columns x
+// 16 rows (variant 0) or 8 rows (variant 1); f32_grid = number of CTAs (and
+// of diagnostics partial records); f32_box = the TMA box of one tile.
+void f32_tiles(int nx, int ny, int variant, int* tiles_x, int* ntiles);
+int f32_grid(int nx, int ny, int variant);
+void f32_box(int variant, unsigned* bx, unsigned* by, unsigned* bz);
+cudaError_t launch_step_f32(const CUtensorMap& in_map, const StepConst<float>& c, const Geom& g, float* out,
+                            double* diag_partials, int* err, long long spin_limit, int inject, int variant,
+                            cudaStream_t stream);
+cudaError_t launch_diag_f32(const StepConst<float>& c, const Geom& g, const float* f, double* partials, int variant,
+                            cudaStream_t s);
 
 // f := f^(0)(fields) on the interior, with ghost images (klb_aux.cu).
 template <typename T>

@@ -142,8 +142,11 @@ __global__ void __launch_bounds__(TX* TY) step_kernel(const __grid_constant__ CU
                                                       int* __restrict__ err, long long spin_limit, int inject) {
     using L = SmemLayout<T, TX, TY>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    T* tile = reinterpret_cast<T*>(smem_raw);
-    T* hx = reinterpret_cast<T*>(smem_raw + L::TILE_BYTES);
+    // 128 spare bytes are reserved so that the TMA destination starts on a
+    // 128-byte boundary of the shared window
+    unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    T* tile = reinterpret_cast<T*>(base);
+    T* hx = reinterpret_cast<T*>(base + L::TILE_BYTES);
     T* hy = hx + L::HX;
     __shared__ __align__(8) uint64_t bar;
     __shared__ __align__(8) uint64_t never;  // fault injection: a barrier nothing arrives on
@@ -196,7 +199,7 @@ cudaError_t launch_step_impl(const CUtensorMap& in_map, const StepConst<T>& c, c
                              cudaStream_t stream) {
     using TT = StepTile<T>;
     constexpr int TX = TT::TX, TY = TT::TY;
-    const size_t smem = SmemLayout<T, TX, TY>::BYTES;
+    const size_t smem = SmemLayout<T, TX, TY>::BYTES + 128;
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(step_kernel<T, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -1,20 +1,367 @@
-// klb_step_f32.cu -- FP32 instantiation of the fused step (production path).
-#include "klb_step.cuh"
+// klb_step_f32.cu -- the fused FDLB time step in FP32 (production path).
+//
+// One launch = one forward-Euler step (Eq. 47 of arXiv:1010.4124) over the
+// whole grid.  Design, chosen so that every WENO5 face flux is evaluated
+// once, occupancy stays high and barriers are few:
+//
+//  * Persistent CTAs (one per SM, 16 warps) walk a list of tiles of 31
+//    columns x 16 rows.  Warp w owns tile row w; lane L owns column x0 + L.
+//  * Each tile (all 19 planes plus a 3-node halo, up to 4 columns on the left
+//    so the box starts on a 16-byte boundary) arrives by one 3-D TMA box load
+//    (plain cp.async.bulk.tensor, no multicast) into one of two shared-memory
+//    buffers; the load of the next tile is issued before the current one is
+//    computed, so copies overlap computation.  Waits are bounded.
+//  * x fluxes: lane L evaluates the face on the LEFT of its column; its right
+//    face is lane L+1's left face, taken with one shuffle.  Lane 31 only
+//    supplies that face (31 output columns per warp).
+//  * y fluxes: each thread evaluates the face BELOW its node and leaves it in
+//    shared memory; the faces above the tile's top row are evaluated by 12
+//    warps (one velocity each); after one barrier each node reads the face
+//    above it from its upper neighbour.
+//  * Per node: moments, F_k, f^(0) and the conservative BGK relaxation
+//    (ArithF32::collide) in registers, the flux divergence, and a coalesced
+//    store; nodes next to a periodic or outflow side also write their ghost
+//    images.  Optionally the diagnostics of the input nodes are reduced (FP64)
+//    per CTA; the stand-alone kernel below reproduces the same order.
+#include "klb_device.cuh"
+#include "klb_launch.h"
 
 namespace fdlb {
-template <>
-cudaError_t launch_step<float>(const CUtensorMap& in_map, const StepConst<float>& c, const Geom& g, float* out,
-                               double* diag_partials, int* err, long long spin_limit, int inject,
-                               cudaStream_t stream) {
-    return launch_step_impl<float>(in_map, c, g, out, diag_partials, err, spin_limit, inject, stream);
+
+namespace v3 {
+constexpr int TW = 31;   // output columns per tile (one warp row)
+constexpr int SXB = 44;  // box width: 31 + 3 + 3 halo + up to 3 columns of 16-byte alignment, x4
+constexpr int NYV = 12;  // velocities with a y component
+static_assert((sizeof(float) * SXB) % 16 == 0, "box rows of 16-byte multiples");
+// tile of TW columns x TY rows (TY warps per CTA, 16 / TY CTAs per SM)
+template <int TY>
+struct Shape {
+    static constexpr int NT = 32 * TY;
+    static constexpr int SYB = TY + 6;  // box height
+    static constexpr int PLANE = SXB * SYB;
+    static constexpr int BOX_FLOATS = NQ * PLANE;
+    static constexpr int BUF_FLOATS = (BOX_FLOATS + 31) / 32 * 32;  // 128-byte multiple (TMA destination)
+    static constexpr int YF_FLOATS = NYV * (TY + 1) * 32;
+    static constexpr size_t SMEM_BYTES = sizeof(float) * (2 * BUF_FLOATS + YF_FLOATS) + 128;
+    static_assert((sizeof(float) * BUF_FLOATS) % 128 == 0, "TMA destination must stay 128-byte aligned");
+};
+}  // namespace v3
+
+// index of velocity q among the 12 with a non-zero y component
+__host__ __device__ constexpr int yslot(int q) {
+    int n = 0;
+    for (int k = 1; k < q; ++k) n += sgn_y(k) != 0 ? 1 : 0;
+    return n;
 }
-void step_tile_shape(int precision, int* tx, int* ty) {
-    if (precision == 1) {
-        *tx = StepTile<double>::TX;
-        *ty = StepTile<double>::TY;
+// the velocity in y slot k
+__host__ __device__ constexpr int yvel(int k) {
+    int n = 0;
+    for (int q = 1; q < NQ; ++q)
+        if (sgn_y(q) != 0) {
+            if (n == k) return q;
+            ++n;
+        }
+    return -1;
+}
+
+// the five upwind-ordered stencil values of the x-face on the left of smem
+// column s in row r of plane P
+template <int SGN>
+__device__ __forceinline__ void xst(const float* P, int r, int s, float v[5]) {  // (independent of TY)
+    const float* a = P + r * v3::SXB + s;
+    if (SGN > 0) {
+        v[0] = a[-3]; v[1] = a[-2]; v[2] = a[-1]; v[3] = a[0]; v[4] = a[1];
     } else {
-        *tx = StepTile<float>::TX;
-        *ty = StepTile<float>::TY;
+        v[0] = a[2]; v[1] = a[1]; v[2] = a[0]; v[3] = a[-1]; v[4] = a[-2];
     }
 }
+// ... of the y-face below smem row r (between rows r-1 and r) of column s
+template <int SGN>
+__device__ __forceinline__ void yst(const float* P, int r, int s, float v[5]) {
+    const float* a = P + r * v3::SXB + s;
+    constexpr int S = v3::SXB;
+    if (SGN > 0) {
+        v[0] = a[-3 * S]; v[1] = a[-2 * S]; v[2] = a[-S]; v[3] = a[0]; v[4] = a[S];
+    } else {
+        v[0] = a[2 * S]; v[1] = a[S]; v[2] = a[0]; v[3] = a[-S]; v[4] = a[-2 * S];
+    }
+}
+__device__ __forceinline__ float2 weno_pair(const float u[5], const float w[5], float eu, float ew) {
+    return ArithF32::weno2(make_float2(u[0], w[0]), make_float2(u[1], w[1]), make_float2(u[2], w[2]),
+                           make_float2(u[3], w[3]), make_float2(u[4], w[4]), make_float2(eu, ew));
+}
+
+// pass A for velocity Q with both components: its x-face and its y-face in
+// one packed evaluation; x flux into post[Q], bottom y-face into shared memory
+template <int TY, int Q>
+__device__ __forceinline__ void pass_a_xy(const StepConst<float>& c, const float* tile, float* yf, int r, int s,
+                                          int ty, int lane, float* post) {
+    constexpr int SGX = sgn_x(Q), SGY = sgn_y(Q);
+    static_assert(SGX != 0 && SGY != 0, "velocity with two components");
+    const float* P = tile + Q * v3::Shape<TY>::PLANE;
+    float u[5], w[5];
+    xst<SGX>(P, r, s, u);
+    yst<SGY>(P, r, s, w);
+    const float2 h = weno_pair(u, w, c.ex[Q], c.ey[Q]);
+    const float hr = __shfl_down_sync(0xffffffffu, h.x, 1);
+    post[Q] -= c.cx[Q] * (hr - h.x);
+    yf[(yslot(Q) * (TY + 1) + ty) * 32 + lane] = h.y;
+}
+// pass A for two velocities QA, QB with an x component only
+template <int TY, int QA, int QB>
+__device__ __forceinline__ void pass_a_xx(const StepConst<float>& c, const float* tile, int r, int s, float* post) {
+    static_assert(sgn_y(QA) == 0 && sgn_y(QB) == 0, "x-only velocities");
+    float u[5], w[5];
+    xst<sgn_x(QA)>(tile + QA * v3::Shape<TY>::PLANE, r, s, u);
+    xst<sgn_x(QB)>(tile + QB * v3::Shape<TY>::PLANE, r, s, w);
+    const float2 h = weno_pair(u, w, c.ex[QA], c.ex[QB]);
+    const float ra = __shfl_down_sync(0xffffffffu, h.x, 1);
+    const float rb = __shfl_down_sync(0xffffffffu, h.y, 1);
+    post[QA] -= c.cx[QA] * (ra - h.x);
+    post[QB] -= c.cx[QB] * (rb - h.y);
+}
+
+// the faces above the tile's top row, velocity of y slot K, for lane's column
+template <int TY, int K>
+__device__ __forceinline__ void top_face(const StepConst<float>& c, const float* tile, float* yf, int s, int lane) {
+    constexpr int Q = yvel(K);
+    constexpr int SGY = sgn_y(Q);
+    float u[5];
+    yst<SGY>(tile + Q * v3::Shape<TY>::PLANE, TY + 3, s, u);
+    yf[(K * (TY + 1) + TY) * 32 + lane] = ArithF32::weno(u[0], u[1], u[2], u[3], u[4], c.ey[Q]);
+}
+// warp w evaluates the top faces of y slots w, w + TY, ... (12 slots)
+template <int TY, int K>
+__device__ __forceinline__ void top_faces(const StepConst<float>& c, const float* tile, float* yf, int s, int lane,
+                                          int w) {
+    if constexpr (K < v3::NYV) {
+        if (w == K % TY) top_face<TY, K>(c, tile, yf, s, lane);
+        top_faces<TY, K + 1>(c, tile, yf, s, lane, w);
+    }
+}
+
+struct TileInfo {
+    int x0, y0, bxa;
+};
+template <int TY>
+__device__ __forceinline__ TileInfo tile_info(int t, int tiles_x) {
+    TileInfo ti;
+    ti.x0 = (t % tiles_x) * v3::TW;
+    ti.y0 = (t / tiles_x) * TY;
+    ti.bxa = ti.x0 & ~3;  // array column of the box start (interior x0 - 4 is array x0): 16-byte aligned
+    return ti;
+}
+
+template <int TY>
+__global__ void __launch_bounds__(32 * TY, 16 / TY) step_f32_kernel(const __grid_constant__ CUtensorMap in_map,
+                                                             const __grid_constant__ StepConst<float> c,
+                                                             const Geom g, int tiles_x, int ntiles,
+                                                             float* __restrict__ out,
+                                                             double* __restrict__ diag_partials,
+                                                             int* __restrict__ err, long long spin_limit,
+                                                             int inject) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // the launch reserves 128 spare bytes so that the buffers start on a
+    // 128-byte boundary of the shared window whatever precedes them
+    float* buf = reinterpret_cast<float*>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
+    using S = v3::Shape<TY>;
+    float* yf = buf + 2 * S::BUF_FLOATS;
+    __shared__ __align__(8) uint64_t full[2];
+    __shared__ __align__(8) uint64_t never;  // fault injection: a barrier nothing arrives on
+
+    const int tid = threadIdx.x, ty = tid >> 5, lane = tid & 31;
+    auto issue = [&](int t, int b) {
+        const TileInfo ti = tile_info<TY>(t, tiles_x);
+        const uint32_t bar = smem_u32(&full[b]);
+        mbar_arrive_expect_tx(bar, (uint32_t)(sizeof(float) * S::BOX_FLOATS));
+        tma_load_3d(smem_u32(buf + b * S::BUF_FLOATS), &in_map, ti.bxa, ti.y0, 0, bar);
+    };
+    if (tid == 0) {
+        mbar_init(smem_u32(&full[0]), 1);
+        mbar_init(smem_u32(&full[1]), 1);
+        mbar_init(smem_u32(&never), 1);
+        fence_barrier_init();
+        fence_proxy_async();
+        if ((int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+    }
+    __syncthreads();
+
+    double dv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const bool diag = diag_partials != nullptr;
+    int k = 0;  // local tile counter: buffer k & 1, phase (k >> 1) & 1
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
+        const int b = k & 1;
+        // prefetch the next tile into the other buffer (freed by the barrier
+        // that closed the previous tile)
+        if (tid == 0 && t + (int)gridDim.x < ntiles) {
+            fence_proxy_async();
+            issue(t + gridDim.x, b ^ 1);
+        }
+        bool late = !mbar_wait_bounded(smem_u32(&full[b]), (k >> 1) & 1, spin_limit);
+        if (inject) late = late || !mbar_wait_bounded(smem_u32(&never), 0, spin_limit);
+        if (__syncthreads_or(late)) {
+            if (tid == 0) {
+                atomicOr(err, ERR_TIMEOUT);
+                // let both copies that may be in flight land before leaving
+                mbar_wait_bounded(smem_u32(&full[b]), (k >> 1) & 1, kDrainPolls);
+                if (t + (int)gridDim.x < ntiles)
+                    mbar_wait_bounded(smem_u32(&full[b ^ 1]), ((k + 1) >> 1) & 1, kDrainPolls);
+            }
+            __syncthreads();
+            return;
+        }
+        const float* tile = buf + b * S::BUF_FLOATS;
+        const TileInfo ti = tile_info<TY>(t, tiles_x);
+        const int ix = ti.x0 + lane, iy = ti.y0 + ty;
+        const int s = lane + 4 + (ti.x0 - ti.bxa);  // smem column of the node
+        const int r = ty + 3;                         // smem row of the node
+        const bool active = lane < v3::TW && ix < g.nx && iy < g.ny;
+
+        float f[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) f[q] = tile[q * S::PLANE + r * v3::SXB + s];
+        const NodeEq<float> st = ArithF32::node_state(c, f);
+        if (diag) {
+            double v[8];
+            node_diag(st, active, v);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) dv[j] = (j == 4 || j == 5 || j == 7) ? fmax(dv[j], v[j]) : dv[j] + v[j];
+        }
+        ArithF32::collide(c, st, f);  // f <- post-collision values
+        // x and y faces of the 12 velocities with two components, packed in pairs
+        pass_a_xy<TY, 1>(c, tile, yf, r, s, ty, lane, f);
+        pass_a_xy<TY, 2>(c, tile, yf, r, s, ty, lane, f);
+        pass_a_xy<TY, 4>(c, tile, yf, r, s, ty, lane, f);
+        pass_a_xy<TY, 5>(c, tile, yf, r, s, ty, lane, f);
+        pass_a_xy<TY, 7>(c, tile, yf, r, s, ty, lane, f);
+        pass_a_xy<TY, 8>(c, tile, yf, r, s, ty, lane, f);
+        pass_a_xy<TY, 10>(c, tile, yf, r, s, ty, lane, f);
+        pass_a_xy<TY, 11>(c, tile, yf, r, s, ty, lane, f);
+        pass_a_xy<TY, 13>(c, tile, yf, r, s, ty, lane, f);
+        pass_a_xy<TY, 14>(c, tile, yf, r, s, ty, lane, f);
+        pass_a_xy<TY, 16>(c, tile, yf, r, s, ty, lane, f);
+        pass_a_xy<TY, 17>(c, tile, yf, r, s, ty, lane, f);
+        // x faces of the six velocities along the x axis, in pairs
+        pass_a_xx<TY, 3, 6>(c, tile, r, s, f);
+        pass_a_xx<TY, 9, 12>(c, tile, r, s, f);
+        pass_a_xx<TY, 15, 18>(c, tile, r, s, f);
+        top_faces<TY, 0>(c, tile, yf, s, lane, ty);  // faces above the tile's top row
+        __syncthreads();
+        // y fluxes from the faces below and above each node
+#pragma unroll
+        for (int q = 1; q < NQ; ++q) {
+            if (sgn_y(q) != 0) {
+                const float* col = yf + (yslot(q) * (TY + 1) + ty) * 32 + lane;
+                f[q] -= c.cy[q] * (col[32] - col[0]);
+            }
+        }
+        if (active) {
+            float* o = out + (long long)(iy + GY) * g.px + (ix + GX);
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) o[q * g.plane] = f[q];
+            if (has_images(g, ix, iy)) {
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) write_images(out, g, q, ix, iy, f[q]);
+            }
+        }
+        __syncthreads();  // the tile buffer and the face buffer are free again
+    }
+    if (diag) diag_block_reduce<S::NT>(dv, diag_partials + 8ll * blockIdx.x);
+}
+
+// Stand-alone diagnostics of a state with the same tiles, per-CTA tile order
+// and block reduction as the fused path, so that both give the same bits.
+template <int TY>
+__global__ void __launch_bounds__(32 * TY) diag_f32_kernel(const StepConst<float> c, const Geom g, int tiles_x,
+                                                           int ntiles, const float* __restrict__ f,
+                                                           double* __restrict__ partials) {
+    const int tid = threadIdx.x, ty = tid >> 5, lane = tid & 31;
+    double dv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const TileInfo ti = tile_info<TY>(t, tiles_x);
+        const int ix = ti.x0 + lane, iy = ti.y0 + ty;
+        const bool active = lane < v3::TW && ix < g.nx && iy < g.ny;
+        float fl[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+            fl[q] = active ? f[q * g.plane + (long long)(iy + GY) * g.px + (ix + GX)] : 1.f;
+        const NodeEq<float> st = ArithF32::node_state(c, fl);
+        double v[8];
+        node_diag(st, active, v);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) dv[j] = (j == 4 || j == 5 || j == 7) ? fmax(dv[j], v[j]) : dv[j] + v[j];
+    }
+    diag_block_reduce<32 * TY>(dv, partials + 8ll * blockIdx.x);
+}
+
+static int num_sms() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+// tile heights offered: 16 rows (one CTA of 16 warps per SM) or 8 rows (two
+// CTAs of 8 warps per SM, whose phases interleave)
+static int rows_of(int variant) { return variant == 1 ? 8 : 16; }
+
+void f32_tiles(int nx, int ny, int variant, int* tiles_x, int* ntiles) {
+    const int ty = rows_of(variant);
+    *tiles_x = (nx + v3::TW - 1) / v3::TW;
+    *ntiles = *tiles_x * ((ny + ty - 1) / ty);
+}
+int f32_grid(int nx, int ny, int variant) {
+    int tx, nt;
+    f32_tiles(nx, ny, variant, &tx, &nt);
+    const int n = num_sms() * (16 / rows_of(variant));
+    return nt < n ? nt : n;
+}
+void f32_box(int variant, unsigned* bx, unsigned* by, unsigned* bz) {
+    *bx = v3::SXB;
+    *by = rows_of(variant) + 6;
+    *bz = NQ;
+}
+
+template <int TY>
+static cudaError_t launch_f32(const CUtensorMap& in_map, const StepConst<float>& c, const Geom& g, float* out,
+                              double* diag_partials, int* err, long long spin_limit, int inject, int variant,
+                              cudaStream_t stream) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(step_f32_kernel<TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)v3::Shape<TY>::SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    int tiles_x, ntiles;
+    f32_tiles(g.nx, g.ny, variant, &tiles_x, &ntiles);
+    step_f32_kernel<TY><<<f32_grid(g.nx, g.ny, variant), 32 * TY, v3::Shape<TY>::SMEM_BYTES, stream>>>(
+        in_map, c, g, tiles_x, ntiles, out, diag_partials, err, spin_limit, inject);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_f32(const CUtensorMap& in_map, const StepConst<float>& c, const Geom& g, float* out,
+                            double* diag_partials, int* err, long long spin_limit, int inject, int variant,
+                            cudaStream_t stream) {
+    if (rows_of(variant) == 8)
+        return launch_f32<8>(in_map, c, g, out, diag_partials, err, spin_limit, inject, variant, stream);
+    return launch_f32<16>(in_map, c, g, out, diag_partials, err, spin_limit, inject, variant, stream);
+}
+
+cudaError_t launch_diag_f32(const StepConst<float>& c, const Geom& g, const float* f, double* partials, int variant,
+                            cudaStream_t s) {
+    int tiles_x, ntiles;
+    f32_tiles(g.nx, g.ny, variant, &tiles_x, &ntiles);
+    const int grid = f32_grid(g.nx, g.ny, variant);
+    if (rows_of(variant) == 8)
+        diag_f32_kernel<8><<<grid, 256, 0, s>>>(c, g, tiles_x, ntiles, f, partials);
+    else
+        diag_f32_kernel<16><<<grid, 512, 0, s>>>(c, g, tiles_x, ntiles, f, partials);
+    return cudaGetLastError();
+}
+
 }  // namespace fdlb

@@ -10,4 +10,8 @@ cudaError_t launch_step<double>(const CUtensorMap& in_map, const StepConst<doubl
                                 cudaStream_t stream) {
     return launch_step_impl<double>(in_map, c, g, out, diag_partials, err, spin_limit, inject, stream);
 }
+void f64_tile(int* tx, int* ty) {
+    *tx = StepTile<double>::TX;
+    *ty = StepTile<double>::TY;
+}
 }  // namespace fdlb

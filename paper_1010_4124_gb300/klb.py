@@ -73,6 +73,8 @@ def lib():
                                      C.POINTER(i32)]),
             "klb_launch_count": (i64, [vp]),
             "klb_debug_inject_wait_timeout": (C.c_int, [vp, i64]),
+            "klb_set_variant": (C.c_int, [vp, C.c_int]),
+            "klb_get_variant": (C.c_int, [vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -213,6 +215,14 @@ class Klb:
         _check(self.h, lib().klb_layout(self.h, C.byref(base), C.byref(pitch), C.byref(plane), C.byref(gx),
                                         C.byref(gy)))
         return base.value, pitch.value, plane.value, gx.value, gy.value
+
+    @property
+    def variant(self) -> int:
+        return int(lib().klb_get_variant(self.h))
+
+    @variant.setter
+    def variant(self, v: int):
+        _check(self.h, lib().klb_set_variant(self.h, int(v)))
 
     def debug_inject_wait_timeout(self, polls: int):
         _check(self.h, lib().klb_debug_inject_wait_timeout(self.h, int(polls)))

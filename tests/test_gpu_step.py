@@ -192,7 +192,8 @@ def test_roofline_4096_windows_parity():
         ref = core.step(pw, win)[:, 3:-3, 3:-3]
         got = fb[:, y0:y0 + W, x0:x0 + W]
         assert rel_err_global(got, ref) <= 1e-5, (y0, x0)
-        errs = rel_err_fields(got, ref, pw)
+        pc = core.Params(nx=W, ny=W, dx=pb.dx, dy=pb.dy, dt=pb.dt, tau=pb.tau)
+        errs = rel_err_fields(got, ref, pc)
         assert max(errs["rho"], errs["u"], errs["T"]) <= 1e-5, ((y0, x0), errs)
 
 
@@ -304,3 +305,19 @@ def test_khi512_growth_rate_matches_oracle(prec):
         for k in range(7):
             scale = np.abs(dref[:, 0 if k in (1, 2) else k]).max()
             assert np.abs(d[:, k] - dref[:, k]).max() <= 1e-12 * scale, k
+
+
+def test_fp32_variants_are_bitwise_identical():
+    # the two tile shapes of the FP32 kernel compute every node with the same
+    # arithmetic: the states agree bit for bit
+    pb = inputs.khi(300, 170, 30)
+    fields = inputs.fields(pb)
+    out = []
+    for v in (0, 1):
+        with gpu_handle(pb, "fp32") as h:
+            h.variant = v
+            assert h.variant == v
+            h.init_fields(*fields)
+            h.step(30)
+            out.append(h.get_f())
+    assert np.array_equal(out[0], out[1])
