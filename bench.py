@@ -263,6 +263,8 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    if rank == 0 and not args.no_sweep:
+        line["sweep"] = sweep_measure(args.sweep_steps, torch)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, samples=3)
     if rank == 0:
@@ -270,6 +272,59 @@ def run_ours(args):
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def sweep_measure(steps: int, torch):
+    """The batched D_v x D_rho sweep (32 KHI instances on uneven grids drawn by
+    seed, FP32, diagnostics every 10 steps): one persistent launch per step
+    over all instances, replayed from a CUDA graph, tiles picked by the
+    autotuner -- against looping the plain single-grid step over the 32
+    instances one after another on the same GPU."""
+    import numpy as np
+    from paper_1010_4124_gb300 import inputs, klb
+    pbs = inputs.sweep_instances(steps)
+    fields = [[np.ascontiguousarray(a) for a in inputs.fields(pb)] for pb in pbs]
+    cells = sum(pb.nx * pb.ny for pb in pbs)
+    stream = torch.cuda.Stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with klb.KlbBatch.from_problems(pbs, stream=stream.cuda_stream) as bt:
+        for m, fl in zip(bt.members, fields):
+            m.init_fields(*fl)
+        variant = bt.autotune(steps=5)
+        bt.step(70)  # warm-up: builds and replays the graph once
+        bt.sync()
+        n0 = bt.launch_count
+        e0.record(stream)
+        bt.step(steps)
+        e1.record(stream)
+        e1.synchronize()
+        bt.sync()
+        t_batch = e0.elapsed_time(e1) * 1e-3
+        launches = bt.launch_count - n0
+        tiles = bt.tiles
+    # the plain step, looped over the instances
+    hs = []
+    for pb, fl in zip(pbs, fields):
+        h = klb.Klb.from_problem(pb, precision="fp32", stream=stream.cuda_stream)
+        h.init_fields(*fl)
+        h.step(3)
+        hs.append(h)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for h in hs:
+        h.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    t_loop = e0.elapsed_time(e1) * 1e-3
+    for h in hs:
+        h.sync()
+        h.close()
+    return {"instances": len(pbs), "cells": cells, "steps": steps, "kernel_variant": variant,
+            "tiles_per_launch": tiles, "launches": launches,
+            "batched_gcell_s": round(cells * steps / t_batch / 1e9, 4),
+            "looped_plain_gcell_s": round(cells * steps / t_loop / 1e9, 4),
+            "speedup_vs_looped_plain": round(t_loop / t_batch, 3),
+            "sizes": sorted({f"{pb.nx}x{pb.ny}" for pb in pbs})}
 
 
 def _band(pb, rows: int):
@@ -353,6 +408,8 @@ def main():
     ap.add_argument("--variant", type=int, default=-1,
                     help="FP32 kernel tile shape (0: 31x16, 1: 31x8); -1 picks the faster by timing both")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--sweep-steps", type=int, default=280)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

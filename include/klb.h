@@ -165,6 +165,60 @@ int64_t klb_launch_count(const klb_t* h);
 int klb_set_variant(klb_t* h, int variant);
 int klb_get_variant(const klb_t* h);
 
+/* ---------------------------------------------------------------------------
+ * Batched engine (the D_v x D_rho sweeps of Sec. IV).  A batch holds n FP32
+ * grids that share the step constants (dx, dy, dt, tau, v, eps) but may differ
+ * in size, boundaries, initial fields and diagnostics cadence.  One launch of
+ * the persistent step kernel advances every grid by one step (the grids' tiles
+ * form one work list, so uneven sizes balance over the GPU); klb_batch_step
+ * replays the step loop from a CUDA graph of whole sampling periods.
+ * ------------------------------------------------------------------------- */
+typedef struct klb_batch klb_batch_t;
+
+/* Create a batch of n grids (params p[0..n-1]; precision must be FP32; the
+ * stream of p[0], or a stream owned by the batch when NULL, serves all of
+ * them).  Errors: KLB_E_INVAL (n < 1 or n > 256, differing constants),
+ * KLB_E_NOMEM, KLB_E_CUDA; the message is klb_batch_last_error(NULL). */
+int klb_batch_create(const klb_params* p, int n, klb_batch_t** out);
+void klb_batch_destroy(klb_batch_t* b); /* NULL-safe; destroys the members */
+int klb_batch_size(const klb_batch_t* b);
+
+/* Borrowed handle of member i (0 <= i < n), owned by the batch: use it for
+ * klb_init_fields, klb_set_f, klb_get_f, klb_moments, klb_diagnostics,
+ * klb_save.  Do not destroy it and do not step it alone (klb_batch_step
+ * requires all members at the same step).  NULL if i is out of range. */
+klb_t* klb_batch_member(klb_batch_t* b, int i);
+
+/* Enqueue n steps of every member and return without waiting.  Diagnostics
+ * of each member are sampled on its own cadence, as klb_step does.  Errors:
+ * KLB_E_STATE (a member not initialised, or members at different steps),
+ * KLB_E_INVAL, KLB_E_CUDA. */
+int klb_batch_step(klb_batch_t* b, int64_t n);
+
+/* Wait for the batch's stream; report device-side errors of the batched step
+ * (KLB_E_DEVICE_TIMEOUT) and of the members (as klb_sync). */
+int klb_batch_sync(klb_batch_t* b);
+
+/* Tile shape of the batched FP32 kernel (as klb_set_variant) for all members. */
+int klb_batch_set_variant(klb_batch_t* b, int variant);
+int klb_batch_get_variant(const klb_batch_t* b);
+
+/* Autotuner: times `steps` batched launches of each tile shape on the
+ * members' current state, keeps the fastest (returned in *variant when not
+ * NULL) and restores the state, so the run continues exactly as if it had not
+ * been called.  Synchronises.  Needs temporary device memory for one copy of
+ * every member's state (KLB_E_NOMEM otherwise). */
+int klb_batch_autotune(klb_batch_t* b, int steps, int* variant);
+
+/* Graph replay on (1, default) or off (0; one launch sequence per call). */
+int klb_batch_use_graph(klb_batch_t* b, int on);
+
+/* Kernel launches enqueued by the batch (graph replays count their kernels);
+ * tiles of one batched launch. */
+int64_t klb_batch_launch_count(const klb_batch_t* b);
+int64_t klb_batch_tiles(const klb_batch_t* b);
+const char* klb_batch_last_error(const klb_batch_t* b);
+
 /* Fault injection for tests.  With polls > 0, every later step launch also
  * waits, with a budget of `polls` polls, on a device barrier that nothing
  * arrives on (a flag that nothing sets): the wait runs out, each CTA records

@@ -8,8 +8,8 @@ KLB_AUX_INST(float)
 
 // One block folds all partial records, in record order per thread and a fixed
 // tree across threads.
-__global__ void diag_finalize_kernel(const double* __restrict__ partials, int nparts, double* __restrict__ out,
-                                     int* __restrict__ err) {
+__global__ void diag_finalize_kernel(const double* __restrict__ partials, int nparts, double* __restrict__ ring,
+                                     int cap, long long* __restrict__ counter, int* __restrict__ err) {
     __shared__ double red[256][8];
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
@@ -34,13 +34,17 @@ __global__ void diag_finalize_kernel(const double* __restrict__ partials, int np
         __syncthreads();
     }
     if (threadIdx.x == 0) {
+        const long long n = *counter;
+        double* out = ring + 7 * (n % cap);
         for (int k = 0; k < 7; ++k) out[k] = red[0][k];
+        *counter = n + 1;
         if (red[0][7] != 0.0) atomicOr(err, ERR_NONFINITE);
     }
 }
 
-cudaError_t launch_diag_finalize(const double* partials, int nparts, double* out, int* err, cudaStream_t s) {
-    diag_finalize_kernel<<<1, 256, 0, s>>>(partials, nparts, out, err);
+cudaError_t launch_diag_finalize(const double* partials, int nparts, double* ring, int cap, long long* counter,
+                                 int* err, cudaStream_t s) {
+    diag_finalize_kernel<<<1, 256, 0, s>>>(partials, nparts, ring, cap, counter, err);
     return cudaGetLastError();
 }
 

@@ -8,39 +8,10 @@
 #include <cmath>
 #include <string>
 
-#include "../../include/klb.h"
-#include "klb_launch.h"
+#include "klb_handle.h"
 
 using namespace fdlb;
 
-struct klb {
-    klb_params p{};
-    Geom g{};
-    size_t esize = 0;             // bytes per element of f
-    void* buf[2] = {nullptr, nullptr};
-    int cur = 0;                  // buffer holding the current state
-    CUtensorMap map[2];
-    StepConst<float> cf{};
-    StepConst<double> cd{};
-    double* fields_dev = nullptr; // 4 * nx * ny doubles of staging for host fields
-    double* fdense_dev = nullptr; // 19 * nx * ny doubles of staging for host f (lazy)
-    double* diag_ring = nullptr;  // [cap][7]
-    double* diag_partials = nullptr;
-    int nparts = 0;
-    int cap = 0;
-    int* err_dev = nullptr;
-    int64_t steps = 0;
-    int64_t nsamples = 0;
-    bool pending_sample = false;
-    bool initialized = false;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    int64_t launches = 0;
-    long long spin_limit = kDefaultSpin;
-    int inject = 0;
-    int variant = 0;  // FP32 tile shape (see klb_set_variant)
-    std::string err;
-};
 
 static thread_local std::string g_create_error;
 
@@ -49,6 +20,7 @@ static int fail(klb_t* h, int code, const std::string& msg) {
     else g_create_error = msg;
     return code;
 }
+int fdlb::handle_fail(klb_t* h, int code, const std::string& msg) { return fail(h, code, msg); }
 static int cuda_fail(klb_t* h, cudaError_t e, const char* where) {
     return fail(h, KLB_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
@@ -267,12 +239,15 @@ int klb_create(const klb_params* pin, klb_t** out) {
     if (cudaMalloc(&h->fields_dev, sizeof(double) * 4 * (size_t)p.nx * p.ny) != cudaSuccess ||
         cudaMalloc(&h->diag_ring, sizeof(double) * 7 * (size_t)h->cap) != cudaSuccess ||
         cudaMalloc(&h->diag_partials, sizeof(double) * 8 * (size_t)h->nparts) != cudaSuccess ||
-        cudaMalloc(&h->err_dev, sizeof(int)) != cudaSuccess) {
+        cudaMalloc(&h->err_dev, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&h->nsamp_dev, sizeof(long long)) != cudaSuccess ||
+        (p.precision == KLB_FP32 && cudaMalloc(&h->descs_dev, 2 * sizeof(InstDesc)) != cudaSuccess)) {
         cudaGetLastError();
         fail(nullptr, KLB_E_NOMEM, "cudaMalloc of the staging buffers failed");
         return cleanup(KLB_E_NOMEM);
     }
     cudaMemset(h->err_dev, 0, sizeof(int));
+    cudaMemset(h->nsamp_dev, 0, sizeof(long long));
     if (p.stream) {
         h->stream = (cudaStream_t)p.stream;
     } else {
@@ -284,6 +259,13 @@ int klb_create(const klb_params* pin, klb_t** out) {
     }
     for (int i = 0; i < 2; ++i) {
         int r = make_map(h, h->buf[i], &h->map[i]);
+        if (r != KLB_OK) {
+            g_create_error = h->err;
+            return cleanup(r);
+        }
+    }
+    if (p.precision == KLB_FP32) {
+        int r = fdlb::handle_upload_descs(h);
         if (r != KLB_OK) {
             g_create_error = h->err;
             return cleanup(r);
@@ -307,6 +289,8 @@ void klb_destroy(klb_t* h) {
     if (h->diag_ring) cudaFree(h->diag_ring);
     if (h->diag_partials) cudaFree(h->diag_partials);
     if (h->err_dev) cudaFree(h->err_dev);
+    if (h->nsamp_dev) cudaFree(h->nsamp_dev);
+    if (h->descs_dev) cudaFree(h->descs_dev);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }
@@ -349,10 +333,10 @@ int klb_init_fields(klb_t* h, const double* rho, const double* ux, const double*
                                            (float*)h->buf[1], h->stream);
     }
     if (e != cudaSuccess) return cuda_fail(h, e, "init kernels");
+    CK(h, cudaMemsetAsync(h->nsamp_dev, 0, sizeof(long long), h->stream));
     h->launches += 2;
     h->cur = 0;
     h->steps = 0;
-    h->nsamples = 0;
     h->pending_sample = h->p.sample_every > 0;
     h->initialized = true;
     return KLB_OK;
@@ -426,10 +410,36 @@ int klb_get_f(klb_t* h, double* f, int on_device) {
     return klb_sync(h);
 }
 
+}  // extern "C"
+
 // partial diagnostics records written by one launch of the current kernel
 static int records(const klb_t* h) {
     if (h->p.precision == KLB_FP64) return h->nparts;
     return f32_grid(h->g.nx, h->g.ny, h->variant);
+}
+
+int fdlb::handle_upload_descs(klb_t* h) {
+    if (h->p.precision != KLB_FP32) return KLB_OK;
+    int tiles_x, ntiles;
+    f32_tiles(h->g.nx, h->g.ny, h->variant, &tiles_x, &ntiles);
+    InstDesc d[2];
+    for (int p = 0; p < 2; ++p) {  // descriptor p: the state is in buf[p], the next one goes to buf[1 - p]
+        memset(&d[p], 0, sizeof(InstDesc));
+        d[p].map = h->map[p];
+        d[p].out = (float*)h->buf[1 - p];
+        d[p].g = h->g;
+        d[p].tiles_x = tiles_x;
+        d[p].first_tile = 0;
+    }
+    CK(h, cudaMemcpy(h->descs_dev, d, sizeof(d), cudaMemcpyHostToDevice));
+    h->ntiles = ntiles;
+    return KLB_OK;
+}
+
+void fdlb::handle_after_step(klb_t* h) {
+    h->cur = 1 - h->cur;
+    h->steps += 1;
+    if (h->p.sample_every > 0 && h->steps % h->p.sample_every == 0) h->pending_sample = true;
 }
 
 // one step: optional fused diagnostics of the input state, then ping-pong
@@ -442,23 +452,21 @@ static int one_step(klb_t* h) {
         e = launch_step<double>(h->map[src], h->cd, h->g, (double*)h->buf[dst], parts, h->err_dev, h->spin_limit,
                                 h->inject, h->stream);
     else
-        e = launch_step_f32(h->map[src], h->cf, h->g, (float*)h->buf[dst], parts, h->err_dev, h->spin_limit,
-                            h->inject, h->variant, h->stream);
+        e = launch_step_f32(h->cf, h->descs_dev + src, 1, h->ntiles, parts, h->err_dev, h->spin_limit, h->inject,
+                            h->variant, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "step kernel");
     h->launches += 1;
     if (parts) {
-        e = launch_diag_finalize(parts, records(h), h->diag_ring + 7 * (h->nsamples % h->cap), h->err_dev,
-                                 h->stream);
+        e = launch_diag_finalize(parts, records(h), h->diag_ring, h->cap, h->nsamp_dev, h->err_dev, h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "diagnostics finalize");
         h->launches += 1;
-        h->nsamples += 1;
         h->pending_sample = false;
     }
-    h->cur = dst;
-    h->steps += 1;
-    if (h->p.sample_every > 0 && h->steps % h->p.sample_every == 0) h->pending_sample = true;
+    fdlb::handle_after_step(h);
     return KLB_OK;
 }
+
+extern "C" {
 
 int klb_step(klb_t* h, int64_t n) {
     if (!h) return KLB_E_INVAL;
@@ -471,6 +479,8 @@ int klb_step(klb_t* h, int64_t n) {
     return KLB_OK;
 }
 
+}  // extern "C"
+
 // take the sample of the current state if it is due and no step has taken it
 static int flush_sample(klb_t* h) {
     if (!h->pending_sample) return KLB_OK;
@@ -480,14 +490,22 @@ static int flush_sample(klb_t* h) {
                         : launch_diag_f32(h->cf, h->g, (const float*)h->buf[h->cur], h->diag_partials,
                                           h->variant, h->stream);
     if (e == cudaSuccess)
-        e = launch_diag_finalize(h->diag_partials, records(h), h->diag_ring + 7 * (h->nsamples % h->cap),
-                                 h->err_dev, h->stream);
+        e = launch_diag_finalize(h->diag_partials, records(h), h->diag_ring, h->cap, h->nsamp_dev, h->err_dev,
+                                 h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "diagnostics kernels");
     h->launches += 2;
-    h->nsamples += 1;
     h->pending_sample = false;
     return KLB_OK;
 }
+int fdlb::handle_sample_if_due(klb_t* h) { return flush_sample(h); }
+
+static int read_nsamples(klb_t* h, long long* n) {
+    CK(h, cudaMemcpyAsync(n, h->nsamp_dev, sizeof(long long), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return KLB_OK;
+}
+
+extern "C" {
 
 int klb_moments(klb_t* h, double* rho, double* ux, double* uy, double* T, int on_device) {
     if (!h) return KLB_E_INVAL;
@@ -514,9 +532,12 @@ int klb_diagnostics(klb_t* h, double* out, int64_t cap, int64_t* count) {
     if (!h->initialized) return fail(h, KLB_E_STATE, "klb_diagnostics before klb_init_fields");
     int r = flush_sample(h);
     if (r != KLB_OK) return r;
-    const int64_t avail = std::min<int64_t>(h->nsamples, h->cap);
+    long long ns = 0;
+    r = read_nsamples(h, &ns);
+    if (r != KLB_OK) return r;
+    const int64_t avail = std::min<int64_t>(ns, h->cap);
     const int64_t m = std::min<int64_t>(avail, cap);
-    const int64_t first = h->nsamples - avail;  // oldest retained sample
+    const int64_t first = ns - avail;  // oldest retained sample
     for (int64_t i = 0; i < m; ++i) {
         const int64_t slot = (first + i) % h->cap;
         CK(h, cudaMemcpyAsync(out + 7 * i, h->diag_ring + 7 * slot, 7 * sizeof(double), cudaMemcpyDeviceToHost,
@@ -552,10 +573,11 @@ int klb_set_variant(klb_t* h, int variant) {
         if (r != KLB_OK) {
             h->variant = old;
             for (int j = 0; j < 2; ++j) make_map(h, h->buf[j], &h->map[j]);
+            fdlb::handle_upload_descs(h);
             return r;
         }
     }
-    return KLB_OK;
+    return fdlb::handle_upload_descs(h);
 }
 
 int klb_get_variant(const klb_t* h) { return h ? h->variant : -1; }
@@ -601,8 +623,11 @@ int klb_save(klb_t* h, const char* path) {
     hd.nx = h->g.nx;
     hd.ny = h->g.ny;
     hd.precision = h->p.precision;
+    long long ns = 0;
+    r = read_nsamples(h, &ns);
+    if (r != KLB_OK) return r;
     hd.steps = h->steps;
-    hd.nsamples = h->nsamples;
+    hd.nsamples = ns;
     hd.cap = h->cap;
     hd.pending = h->pending_sample;
     hd.p = h->p;
@@ -638,9 +663,10 @@ int klb_load(klb_t* h, const char* path) {
     CK(h, cudaMemcpy(h->buf[0], blob.data(), fbytes, cudaMemcpyHostToDevice));
     CK(h, cudaMemcpy(h->buf[1], blob.data(), fbytes, cudaMemcpyHostToDevice));
     CK(h, cudaMemcpy(h->diag_ring, ring.data(), ring.size(), cudaMemcpyHostToDevice));
+    const long long ns = hd.nsamples;
+    CK(h, cudaMemcpy(h->nsamp_dev, &ns, sizeof(long long), cudaMemcpyHostToDevice));
     h->cur = 0;
     h->steps = hd.steps;
-    h->nsamples = hd.nsamples;
     h->pending_sample = hd.pending != 0;
     h->initialized = true;
     return KLB_OK;

@@ -28,9 +28,24 @@ void f64_tile(int* tx, int* ty);
 void f32_tiles(int nx, int ny, int variant, int* tiles_x, int* ntiles);
 int f32_grid(int nx, int ny, int variant);
 void f32_box(int variant, unsigned* bx, unsigned* by, unsigned* bz);
-cudaError_t launch_step_f32(const CUtensorMap& in_map, const StepConst<float>& c, const Geom& g, float* out,
+// Descriptor of one grid for the FP32 step: the TMA map of its current state,
+// the buffer that receives the next one, its geometry and the index of its
+// first tile in the launch's tile index space.  Lives in device memory.
+constexpr int kMaxInstances = 256;
+struct alignas(64) InstDesc {
+    CUtensorMap map;
+    float* out;
+    Geom g;
+    int tiles_x;
+    int first_tile;
+};
+// One launch steps every grid of `descs` (ninst entries, ntiles tiles in all).
+// diag_partials (ninst == 1 only) also reduces the diagnostics of the input.
+cudaError_t launch_step_f32(const StepConst<float>& c, const InstDesc* descs, int ninst, int ntiles,
                             double* diag_partials, int* err, long long spin_limit, int inject, int variant,
                             cudaStream_t stream);
+// set the kernels' attributes and query the device once (before any capture)
+cudaError_t prepare_f32_kernels();
 cudaError_t launch_diag_f32(const StepConst<float>& c, const Geom& g, const float* f, double* partials, int variant,
                             cudaStream_t s);
 
@@ -55,7 +70,10 @@ cudaError_t launch_fields(const StepConst<T>& c, const Geom& g, const T* f, doub
 template <typename T>
 cudaError_t launch_diag_partials(const StepConst<T>& c, const Geom& g, const T* f, double* partials,
                                  cudaStream_t s);
-// reduce nparts partial records into ring slot `out` (7 doubles); sets ERR_NONFINITE
-cudaError_t launch_diag_finalize(const double* partials, int nparts, double* out, int* err, cudaStream_t s);
+// reduce nparts partial records into ring slot (*counter % cap) of `ring`
+// (7 doubles per slot), advance *counter; sets ERR_NONFINITE in *err.  The slot
+// is chosen on the device, so the launch can be captured in a CUDA graph.
+cudaError_t launch_diag_finalize(const double* partials, int nparts, double* ring, int cap, long long* counter,
+                                 int* err, cudaStream_t s);
 
 }  // namespace fdlb

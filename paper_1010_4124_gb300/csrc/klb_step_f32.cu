@@ -152,14 +152,31 @@ __device__ __forceinline__ TileInfo tile_info(int t, int tiles_x) {
     return ti;
 }
 
+// Tiles of several instances (grids of one batch, or the single grid of a
+// handle) form one index space: instance i owns tiles [first_i, first_i + n_i).
+// The CTA keeps the first-tile table in shared memory and finds a tile's
+// instance by binary search.
+__device__ __forceinline__ int find_inst(const int* first, int ninst, int t) {
+    int lo = 0, hi = ninst - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (first[mid] <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// acquire a tensor map that the host wrote to global memory before the launch
+__device__ __forceinline__ void tensormap_acquire(const void* map) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
+}
+
 template <int TY>
-__global__ void __launch_bounds__(32 * TY, 16 / TY) step_f32_kernel(const __grid_constant__ CUtensorMap in_map,
-                                                             const __grid_constant__ StepConst<float> c,
-                                                             const Geom g, int tiles_x, int ntiles,
-                                                             float* __restrict__ out,
-                                                             double* __restrict__ diag_partials,
-                                                             int* __restrict__ err, long long spin_limit,
-                                                             int inject) {
+__global__ void __launch_bounds__(32 * TY, 16 / TY) step_f32_kernel(const __grid_constant__ StepConst<float> c,
+                                                                    const InstDesc* __restrict__ descs, int ninst,
+                                                                    int ntiles, double* __restrict__ diag_partials,
+                                                                    int* __restrict__ err, long long spin_limit,
+                                                                    int inject) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // the launch reserves 128 spare bytes so that the buffers start on a
     // 128-byte boundary of the shared window whatever precedes them
@@ -168,14 +185,19 @@ __global__ void __launch_bounds__(32 * TY, 16 / TY) step_f32_kernel(const __grid
     float* yf = buf + 2 * S::BUF_FLOATS;
     __shared__ __align__(8) uint64_t full[2];
     __shared__ __align__(8) uint64_t never;  // fault injection: a barrier nothing arrives on
+    __shared__ int first[kMaxInstances];
 
     const int tid = threadIdx.x, ty = tid >> 5, lane = tid & 31;
+    for (int i = tid; i < ninst; i += blockDim.x) first[i] = descs[i].first_tile;
     auto issue = [&](int t, int b) {
-        const TileInfo ti = tile_info<TY>(t, tiles_x);
+        const InstDesc* D = descs + find_inst(first, ninst, t);
+        const TileInfo ti = tile_info<TY>(t - D->first_tile, D->tiles_x);
         const uint32_t bar = smem_u32(&full[b]);
+        tensormap_acquire(&D->map);
         mbar_arrive_expect_tx(bar, (uint32_t)(sizeof(float) * S::BOX_FLOATS));
-        tma_load_3d(smem_u32(buf + b * S::BUF_FLOATS), &in_map, ti.bxa, ti.y0, 0, bar);
+        tma_load_3d(smem_u32(buf + b * S::BUF_FLOATS), &D->map, ti.bxa, ti.y0, 0, bar);
     };
+    __syncthreads();
     if (tid == 0) {
         mbar_init(smem_u32(&full[0]), 1);
         mbar_init(smem_u32(&full[1]), 1);
@@ -210,8 +232,11 @@ __global__ void __launch_bounds__(32 * TY, 16 / TY) step_f32_kernel(const __grid
             __syncthreads();
             return;
         }
+        const InstDesc* D = descs + find_inst(first, ninst, t);
+        const Geom g = D->g;
+        float* __restrict__ out = D->out;
         const float* tile = buf + b * S::BUF_FLOATS;
-        const TileInfo ti = tile_info<TY>(t, tiles_x);
+        const TileInfo ti = tile_info<TY>(t - D->first_tile, D->tiles_x);
         const int ix = ti.x0 + lane, iy = ti.y0 + ty;
         const int s = lane + 4 + (ti.x0 - ti.bxa);  // smem column of the node
         const int r = ty + 3;                         // smem row of the node
@@ -327,29 +352,45 @@ void f32_box(int variant, unsigned* bx, unsigned* by, unsigned* bz) {
 }
 
 template <int TY>
-static cudaError_t launch_f32(const CUtensorMap& in_map, const StepConst<float>& c, const Geom& g, float* out,
-                              double* diag_partials, int* err, long long spin_limit, int inject, int variant,
-                              cudaStream_t stream) {
-    static bool attr_set = false;
-    if (!attr_set) {
+static cudaError_t set_attr() {
+    static bool done = false;
+    if (!done) {
         cudaError_t e = cudaFuncSetAttribute(step_f32_kernel<TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)v3::Shape<TY>::SMEM_BYTES);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        done = true;
     }
-    int tiles_x, ntiles;
-    f32_tiles(g.nx, g.ny, variant, &tiles_x, &ntiles);
-    step_f32_kernel<TY><<<f32_grid(g.nx, g.ny, variant), 32 * TY, v3::Shape<TY>::SMEM_BYTES, stream>>>(
-        in_map, c, g, tiles_x, ntiles, out, diag_partials, err, spin_limit, inject);
+    return cudaSuccess;
+}
+
+cudaError_t prepare_f32_kernels() {
+    num_sms();
+    cudaError_t e = set_attr<8>();
+    return e != cudaSuccess ? e : set_attr<16>();
+}
+
+template <int TY>
+static cudaError_t launch_f32(const StepConst<float>& c, const InstDesc* descs, int ninst, int ntiles,
+                              double* diag_partials, int* err, long long spin_limit, int inject, int grid,
+                              cudaStream_t stream) {
+    cudaError_t e = set_attr<TY>();
+    if (e != cudaSuccess) return e;
+    step_f32_kernel<TY><<<grid, 32 * TY, v3::Shape<TY>::SMEM_BYTES, stream>>>(c, descs, ninst, ntiles,
+                                                                            diag_partials, err, spin_limit,
+                                                                            inject);
     return cudaGetLastError();
 }
 
-cudaError_t launch_step_f32(const CUtensorMap& in_map, const StepConst<float>& c, const Geom& g, float* out,
+cudaError_t launch_step_f32(const StepConst<float>& c, const InstDesc* descs, int ninst, int ntiles,
                             double* diag_partials, int* err, long long spin_limit, int inject, int variant,
                             cudaStream_t stream) {
+    if (ninst < 1 || ninst > kMaxInstances) return cudaErrorInvalidValue;
+    const int per_sm = 16 / rows_of(variant);
+    const int grid = ntiles < num_sms() * per_sm ? ntiles : num_sms() * per_sm;
+    if (grid < 1) return cudaSuccess;
     if (rows_of(variant) == 8)
-        return launch_f32<8>(in_map, c, g, out, diag_partials, err, spin_limit, inject, variant, stream);
-    return launch_f32<16>(in_map, c, g, out, diag_partials, err, spin_limit, inject, variant, stream);
+        return launch_f32<8>(c, descs, ninst, ntiles, diag_partials, err, spin_limit, inject, grid, stream);
+    return launch_f32<16>(c, descs, ninst, ntiles, diag_partials, err, spin_limit, inject, grid, stream);
 }
 
 cudaError_t launch_diag_f32(const StepConst<float>& c, const Geom& g, const float* f, double* partials, int variant,

@@ -75,6 +75,19 @@ def lib():
             "klb_debug_inject_wait_timeout": (C.c_int, [vp, i64]),
             "klb_set_variant": (C.c_int, [vp, C.c_int]),
             "klb_get_variant": (C.c_int, [vp]),
+            "klb_batch_create": (C.c_int, [C.POINTER(klb_params), C.c_int, C.POINTER(vp)]),
+            "klb_batch_destroy": (None, [vp]),
+            "klb_batch_size": (C.c_int, [vp]),
+            "klb_batch_member": (vp, [vp, C.c_int]),
+            "klb_batch_step": (C.c_int, [vp, i64]),
+            "klb_batch_sync": (C.c_int, [vp]),
+            "klb_batch_set_variant": (C.c_int, [vp, C.c_int]),
+            "klb_batch_get_variant": (C.c_int, [vp]),
+            "klb_batch_autotune": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int)]),
+            "klb_batch_use_graph": (C.c_int, [vp, C.c_int]),
+            "klb_batch_launch_count": (i64, [vp]),
+            "klb_batch_tiles": (i64, [vp]),
+            "klb_batch_last_error": (C.c_char_p, [vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -124,12 +137,17 @@ def make_params(nx, ny, dx, dy, dt, tau, v=(1.0, 2.0, 3.0), bc_x=("periodic", "p
 class Klb:
     """One simulation handle (klb_create ... klb_destroy)."""
 
-    def __init__(self, params: klb_params):
-        h = C.c_void_p()
-        code = lib().klb_create(C.byref(params), C.byref(h))
-        if code != KLB_OK:
-            raise KlbError(code, (lib().klb_last_error(None) or b"").decode())
-        self.h = h
+    def __init__(self, params: klb_params, _borrowed=None):
+        if _borrowed is not None:  # a member of a batch: owned by the batch
+            self.h = C.c_void_p(_borrowed)
+            self._owned = False
+        else:
+            h = C.c_void_p()
+            code = lib().klb_create(C.byref(params), C.byref(h))
+            if code != KLB_OK:
+                raise KlbError(code, (lib().klb_last_error(None) or b"").decode())
+            self.h = h
+            self._owned = True
         self.nx, self.ny = params.nx, params.ny
         self.params = params
 
@@ -141,7 +159,8 @@ class Klb:
 
     def close(self):
         if getattr(self, "h", None):
-            lib().klb_destroy(self.h)
+            if getattr(self, "_owned", True):
+                lib().klb_destroy(self.h)
             self.h = None
 
     def __del__(self):
@@ -226,3 +245,83 @@ class Klb:
 
     def debug_inject_wait_timeout(self, polls: int):
         _check(self.h, lib().klb_debug_inject_wait_timeout(self.h, int(polls)))
+
+
+def _bcheck(b, code):
+    if code != KLB_OK:
+        msg = lib().klb_batch_last_error(b)
+        raise KlbError(code, msg.decode() if msg else "")
+
+
+class KlbBatch:
+    """A batch of FP32 grids stepped together (klb_batch_create ... destroy)."""
+
+    def __init__(self, params_list, stream=None):
+        n = len(params_list)
+        arr = (klb_params * n)(*params_list)
+        if stream is not None:
+            arr[0].stream = stream
+        b = C.c_void_p()
+        code = lib().klb_batch_create(arr, n, C.byref(b))
+        if code != KLB_OK:
+            raise KlbError(code, (lib().klb_batch_last_error(None) or b"").decode())
+        self.b = b
+        self.members = [Klb(params_list[i], _borrowed=lib().klb_batch_member(b, i)) for i in range(n)]
+
+    @classmethod
+    def from_problems(cls, problems, stream=None, **kw):
+        return cls([make_params(pb.nx, pb.ny, pb.dx, pb.dy, pb.dt, pb.tau, v=pb.v, bc_x=pb.bc_x, bc_y=pb.bc_y,
+                                precision="fp32", sample_every=pb.sample_every, **kw) for pb in problems],
+                   stream=stream)
+
+    def close(self):
+        if getattr(self, "b", None):
+            for m in self.members:
+                m.h = None
+            lib().klb_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __len__(self):
+        return len(self.members)
+
+    def step(self, n: int = 1):
+        _bcheck(self.b, lib().klb_batch_step(self.b, int(n)))
+
+    def sync(self):
+        _bcheck(self.b, lib().klb_batch_sync(self.b))
+
+    @property
+    def variant(self) -> int:
+        return int(lib().klb_batch_get_variant(self.b))
+
+    @variant.setter
+    def variant(self, v: int):
+        _bcheck(self.b, lib().klb_batch_set_variant(self.b, int(v)))
+
+    def autotune(self, steps: int = 10) -> int:
+        v = C.c_int(-1)
+        _bcheck(self.b, lib().klb_batch_autotune(self.b, int(steps), C.byref(v)))
+        return v.value
+
+    def use_graph(self, on: bool):
+        _bcheck(self.b, lib().klb_batch_use_graph(self.b, 1 if on else 0))
+
+    @property
+    def launch_count(self) -> int:
+        return int(lib().klb_batch_launch_count(self.b))
+
+    @property
+    def tiles(self) -> int:
+        return int(lib().klb_batch_tiles(self.b))
