@@ -219,6 +219,58 @@ int64_t klb_batch_launch_count(const klb_batch_t* b);
 int64_t klb_batch_tiles(const klb_batch_t* b);
 const char* klb_batch_last_error(const klb_batch_t* b);
 
+/* ---------------------------------------------------------------------------
+ * Adjoint run (reverse-mode sensitivities of the whole time integration).
+ * Objective, from the quantities Sec. IV measures the instability with
+ * (E_x = rho u_y^2 / 2 and its growth coefficient):
+ *   KE    = dx dy sum_nodes rho u_y^2 / 2 after the last step,
+ *   gamma = 1/2 x the least-squares slope of ln K_s against t over the last
+ *           75% of the samples, K_s = sum_nodes rho u_y^2 / 2 of sample s
+ *           (samples every sample_every steps from t = 0),
+ *   L = g_KE KE + g_gamma gamma.
+ * The reverse sweep applies the hand-written transpose of the step's Jacobian
+ * (WENO5 including its nonlinear weights, f^(0) through the moments, BGK),
+ * segment by segment from checkpoints taken every checkpoint_every steps
+ * (the segment's states are recomputed), and ends with the sensitivities of
+ * the initial fields (f^0 = f^(0)(rho, u, T)).
+ * ------------------------------------------------------------------------- */
+typedef struct klb_adj klb_adj_t;
+
+/* A forward grid with params p (FP32 or FP64; periodic or outflow sides only;
+ * sample_every >= 1 dividing nsteps) and room for ceil(nsteps /
+ * checkpoint_every) checkpoints plus one segment of states.
+ * checkpoint_every = 1 stores every state (no recomputation).  Errors:
+ * KLB_E_INVAL, KLB_E_NOMEM, KLB_E_CUDA (message: klb_adjoint_last_error(NULL)). */
+int klb_adjoint_create(const klb_params* p, int64_t nsteps, int32_t checkpoint_every, klb_adj_t** out);
+void klb_adjoint_destroy(klb_adj_t* a); /* NULL-safe */
+
+/* The forward run from the initial fields ([ny][nx] doubles): checkpoints,
+ * samples, and the objective parts *ke and *gamma (either may be NULL).
+ * Synchronises. */
+int klb_adjoint_forward(klb_adj_t* a, const double* rho, const double* ux, const double* uy, const double* T,
+                        int on_device, double* ke, double* gamma);
+
+/* dL/d(rho, u_x, u_y, T) of the initial fields ([ny][nx] doubles, caller
+ * owned) for L = g_ke KE + g_gamma gamma of the last forward run.  Requires a
+ * preceding klb_adjoint_forward (KLB_E_STATE otherwise; the reverse sweep
+ * reuses the forward grid's buffers, so each backward needs its own forward).
+ * Synchronises. */
+int klb_adjoint_backward(klb_adj_t* a, double g_ke, double g_gamma, double* d_rho, double* d_ux, double* d_uy,
+                         double* d_T, int on_device);
+
+/* The bare vector-Jacobian product of the nsteps-step map of the last forward
+ * run: lam_0 = (d f^N / d f^0)^T lam_N, both [19][ny][nx] doubles over the
+ * interior nodes (dependences through ghost nodes folded in).  Requires a
+ * preceding klb_adjoint_forward.  Synchronises. */
+int klb_adjoint_vjp(klb_adj_t* a, const double* lam_N, double* lam_0, int on_device);
+
+/* K_s of the last forward run (up to cap values into out; count in *count). */
+int klb_adjoint_samples(klb_adj_t* a, double* out, int64_t cap, int64_t* count);
+
+/* The forward grid (borrowed; for klb_get_f / klb_moments after a forward). */
+klb_t* klb_adjoint_grid(klb_adj_t* a);
+const char* klb_adjoint_last_error(const klb_adj_t* a);
+
 /* Fault injection for tests.  With polls > 0, every later step launch also
  * waits, with a budget of `polls` polls, on a device barrier that nothing
  * arrives on (a flag that nothing sets): the wait runs out, each CTA records

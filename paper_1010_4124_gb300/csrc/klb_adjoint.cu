@@ -1,0 +1,369 @@
+// klb_adjoint.cu -- the adjoint run: forward with checkpoints, reverse sweep
+// with recomputation per segment, and the sensitivities of the initial
+// fields.  The kernels live in klb_adjoint.cuh.
+//
+// Objective (Sec. IV of arXiv:1010.4124: the perturbation kinetic energy
+// E_x = rho u_y^2 / 2 and the growth coefficient fitted to its logarithm):
+//   KE    = dx dy sum_nodes rho u_y^2 / 2 at the last step,
+//   gamma = (1/2) OLS slope of ln K_s over the fit window (the last 75% of the
+//           samples), K_s = sum_nodes rho u_y^2 / 2 of sample s,
+// L = g_KE KE + g_gamma gamma.  The reverse sweep adds the sources
+// dL/dK_s dK_s/df at the sampled steps.
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "klb_adjoint.cuh"
+#include "klb_handle.h"
+
+using namespace fdlb;
+
+struct klb_adj {
+    klb_t* h = nullptr;            // forward grid (owns the step buffers)
+    int64_t nsteps = 0;
+    int ckpt = 0;                  // steps per checkpoint segment
+    int nck = 0;                   // checkpoints (segment starts)
+    std::vector<void*> ck;         // state at the start of each segment (full buffers)
+    std::vector<void*> seg;        // states of one segment during the reverse sweep (ckpt - 1 extra)
+    void* lam[2] = {nullptr, nullptr};
+    void* Dx = nullptr;
+    void* Dy = nullptr;
+    double* fields = nullptr;      // the initial fields (4 * nx * ny)
+    double* dense = nullptr;       // staging for host / dense arrays (19 * nx * ny)
+    std::vector<double> K;         // K_s of the forward run
+    double ke = 0, gamma = 0;
+    bool forward_done = false;
+    std::string err;
+};
+
+static thread_local std::string g_adj_create_error;
+
+static int afail(klb_adj_t* a, int code, const std::string& msg) {
+    if (a) a->err = msg;
+    else g_adj_create_error = msg;
+    return code;
+}
+#define ACK(a, call)                                                                                          \
+    do {                                                                                                      \
+        cudaError_t e_ = (call);                                                                              \
+        if (e_ != cudaSuccess) return afail(a, KLB_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+static int grid_of(long long n) {
+    long long b = (n + 255) / 256;
+    return (int)std::max<long long>(1, std::min<long long>(b, 152 * 32));
+}
+
+static size_t state_bytes(const klb_t* h) { return (size_t)NQ * h->g.plane * h->esize; }
+
+// one raw step of the forward grid from buf[cur] into buf[1 - cur], no sampling
+static int raw_step(klb_adj_t* a) {
+    klb_t* h = a->h;
+    const int src = h->cur, dst = 1 - h->cur;
+    cudaError_t e;
+    if (h->p.precision == KLB_FP64)
+        e = launch_step<double>(h->map[src], h->cd, h->g, (double*)h->buf[dst], nullptr, h->err_dev, h->spin_limit,
+                                h->inject, h->stream);
+    else
+        e = launch_step_f32(h->cf, h->descs_dev + src, 1, h->ntiles, nullptr, h->err_dev, h->spin_limit, h->inject,
+                            h->variant, h->stream);
+    if (e != cudaSuccess) return afail(a, KLB_E_CUDA, std::string("step kernel: ") + cudaGetErrorString(e));
+    h->cur = dst;
+    h->launches += 1;
+    return KLB_OK;
+}
+
+template <typename T>
+static int vjp_step(klb_adj_t* a, const void* f, const void* lam_in, void* lam_out, double coef) {
+    klb_t* h = a->h;
+    const StepConst<T>& c = *reinterpret_cast<const StepConst<T>*>(sizeof(T) == 8 ? (const void*)&h->cd
+                                                                                   : (const void*)&h->cf);
+    const Geom& g = h->g;
+    adj_faces_x_kernel<T><<<grid_of((long long)(g.nx + 1) * g.ny), 256, 0, h->stream>>>(
+        c, g, (const T*)f, (const T*)lam_in, (T*)a->Dx);
+    adj_faces_y_kernel<T><<<grid_of((long long)g.nx * (g.ny + 1)), 256, 0, h->stream>>>(
+        c, g, (const T*)f, (const T*)lam_in, (T*)a->Dy);
+    adj_gather_kernel<T><<<grid_of((long long)g.nx * g.ny), 256, 0, h->stream>>>(
+        c, g, (const T*)f, (const T*)lam_in, (const T*)a->Dx, (const T*)a->Dy, T(coef), (T*)lam_out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return afail(a, KLB_E_CUDA, std::string("adjoint kernels: ") + cudaGetErrorString(e));
+    h->launches += 3;
+    return KLB_OK;
+}
+
+static int vjp(klb_adj_t* a, const void* f, const void* lam_in, void* lam_out, double coef) {
+    return a->h->p.precision == KLB_FP64 ? vjp_step<double>(a, f, lam_in, lam_out, coef)
+                                         : vjp_step<float>(a, f, lam_in, lam_out, coef);
+}
+
+template <typename T>
+static int source(klb_adj_t* a, const void* f, double coef, void* lam) {
+    klb_t* h = a->h;
+    const StepConst<T>& c = *reinterpret_cast<const StepConst<T>*>(sizeof(T) == 8 ? (const void*)&h->cd
+                                                                                   : (const void*)&h->cf);
+    adj_source_kernel<T><<<grid_of((long long)h->g.nx * h->g.ny), 256, 0, h->stream>>>(c, h->g, (const T*)f, T(coef),
+                                                                                        (T*)lam);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return afail(a, KLB_E_CUDA, std::string("adjoint source: ") + cudaGetErrorString(e));
+    h->launches += 1;
+    return KLB_OK;
+}
+
+// sample index of step n (or -1 when n is not sampled)
+static int sample_of(const klb_adj_t* a, int64_t n) {
+    const int s = a->h->p.sample_every;
+    return (n % s == 0) ? (int)(n / s) : -1;
+}
+
+// dL/dK_s of sample s
+static double dL_dK(const klb_adj_t* a, int s, double g_ke, double g_gamma) {
+    const klb_t* h = a->h;
+    const int M = (int)a->K.size();
+    double d = 0.0;
+    if (s == M - 1) d += g_ke * h->p.dx * h->p.dy;
+    const int start = M - (3 * M) / 4;
+    if (g_gamma != 0.0 && s >= start && M - start >= 2) {
+        // gamma = 1/2 sum_s w_s ln K_s, w_s = (t_s - tbar) / sum (t - tbar)^2
+        const double dt = h->p.dt * h->p.sample_every;
+        double tbar = 0.0;
+        for (int k = start; k < M; ++k) tbar += k * dt;
+        tbar /= (M - start);
+        double sxx = 0.0;
+        for (int k = start; k < M; ++k) sxx += (k * dt - tbar) * (k * dt - tbar);
+        d += g_gamma * 0.5 * ((s * dt - tbar) / sxx) / a->K[s];
+    }
+    return d;
+}
+
+// the reverse sweep from lam[cur_l] = lambda^N down to lambda^0; with
+// objective sources when `sources` is set (g_ke, g_gamma)
+static int reverse(klb_adj_t* a, bool sources, double g_ke, double g_gamma, int* lam_cur) {
+    klb_t* h = a->h;
+    int lc = *lam_cur;
+    for (int s = a->nck - 1; s >= 0; --s) {
+        const int64_t n0 = (int64_t)s * a->ckpt;
+        const int64_t n1 = std::min<int64_t>(n0 + a->ckpt, a->nsteps);
+        const int len = (int)(n1 - n0);
+        // recompute the segment's states f^{n0} .. f^{n1-1} from its checkpoint
+        std::vector<const void*> states(len);
+        states[0] = a->ck[s];
+        if (len > 1) {
+            ACK(a, cudaMemcpyAsync(h->buf[h->cur], a->ck[s], state_bytes(h), cudaMemcpyDeviceToDevice, h->stream));
+            for (int k = 1; k < len; ++k) {
+                int r = raw_step(a);
+                if (r != KLB_OK) return r;
+                ACK(a, cudaMemcpyAsync(a->seg[k - 1], h->buf[h->cur], state_bytes(h), cudaMemcpyDeviceToDevice,
+                                       h->stream));
+                states[k] = a->seg[k - 1];
+            }
+        }
+        for (int64_t n = n1 - 1; n >= n0; --n) {
+            double coef = 0.0;
+            const int si = sample_of(a, n);
+            if (sources && si >= 0) coef = dL_dK(a, si, g_ke, g_gamma);
+            int r = vjp(a, states[n - n0], a->lam[lc], a->lam[1 - lc], coef);
+            if (r != KLB_OK) return r;
+            lc = 1 - lc;
+        }
+    }
+    *lam_cur = lc;
+    return KLB_OK;
+}
+
+template <typename T>
+static int fields_grad(klb_adj_t* a, const void* lam, double* d) {
+    klb_t* h = a->h;
+    const StepConst<T>& c = *reinterpret_cast<const StepConst<T>*>(sizeof(T) == 8 ? (const void*)&h->cd
+                                                                                   : (const void*)&h->cf);
+    const size_t n = (size_t)h->g.nx * h->g.ny;
+    adj_fields_kernel<T><<<grid_of((long long)n), 256, 0, h->stream>>>(
+        c, h->g, a->fields, a->fields + n, a->fields + 2 * n, a->fields + 3 * n, (const T*)lam, d, d + n, d + 2 * n,
+        d + 3 * n);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return afail(a, KLB_E_CUDA, std::string("adjoint fields: ") + cudaGetErrorString(e));
+    h->launches += 1;
+    return KLB_OK;
+}
+
+extern "C" {
+
+int klb_adjoint_create(const klb_params* p, int64_t nsteps, int32_t checkpoint_every, klb_adj_t** out) {
+    if (!p || !out) return afail(nullptr, KLB_E_INVAL, "NULL argument");
+    *out = nullptr;
+    if (nsteps < 1 || checkpoint_every < 1) return afail(nullptr, KLB_E_INVAL, "nsteps and checkpoint_every must be >= 1");
+    if (p->sample_every < 1 || nsteps % p->sample_every != 0)
+        return afail(nullptr, KLB_E_INVAL, "sample_every must be >= 1 and divide nsteps");
+    const int bcs[4] = {p->bc_x_lo, p->bc_x_hi, p->bc_y_lo, p->bc_y_hi};
+    for (int b : bcs)
+        if (b == KLB_BC_FIXED_EQ)
+            return afail(nullptr, KLB_E_INVAL, "the adjoint supports periodic and outflow sides only");
+    klb_params q = *p;
+    q.diag_capacity = (int32_t)(nsteps / p->sample_every + 1);
+    klb_adj_t* a = new klb_adj();
+    a->nsteps = nsteps;
+    a->ckpt = checkpoint_every;
+    a->nck = (int)((nsteps + checkpoint_every - 1) / checkpoint_every);
+    int r = klb_create(&q, &a->h);
+    if (r != KLB_OK) {
+        delete a;
+        return afail(nullptr, r, std::string("forward grid: ") + klb_last_error(nullptr));
+    }
+    klb_t* h = a->h;
+    const size_t sb = state_bytes(h);
+    const size_t nn = (size_t)h->g.nx * h->g.ny;
+    bool ok = true;
+    a->ck.assign(a->nck, nullptr);
+    for (int s = 0; s < a->nck && ok; ++s) ok = cudaMalloc(&a->ck[s], sb) == cudaSuccess;
+    a->seg.assign(std::max(0, a->ckpt - 1), nullptr);
+    for (size_t s = 0; s < a->seg.size() && ok; ++s) ok = cudaMalloc(&a->seg[s], sb) == cudaSuccess;
+    for (int k = 0; k < 2 && ok; ++k) ok = cudaMalloc(&a->lam[k], sb) == cudaSuccess;
+    ok = ok && cudaMalloc(&a->Dx, h->esize * 5 * (size_t)18 * h->g.ny * (h->g.nx + 1)) == cudaSuccess;
+    ok = ok && cudaMalloc(&a->Dy, h->esize * 5 * (size_t)12 * (h->g.ny + 1) * h->g.nx) == cudaSuccess;
+    ok = ok && cudaMalloc(&a->fields, sizeof(double) * 4 * nn) == cudaSuccess;
+    ok = ok && cudaMalloc(&a->dense, sizeof(double) * NQ * nn) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        klb_adjoint_destroy(a);
+        return afail(nullptr, KLB_E_NOMEM, "cudaMalloc of the checkpoints failed");
+    }
+    for (int k = 0; k < 2; ++k) cudaMemset(a->lam[k], 0, sb);
+    *out = a;
+    return KLB_OK;
+}
+
+void klb_adjoint_destroy(klb_adj_t* a) {
+    if (!a) return;
+    if (a->h) cudaStreamSynchronize(a->h->stream);
+    for (void* p : a->ck)
+        if (p) cudaFree(p);
+    for (void* p : a->seg)
+        if (p) cudaFree(p);
+    for (int k = 0; k < 2; ++k)
+        if (a->lam[k]) cudaFree(a->lam[k]);
+    if (a->Dx) cudaFree(a->Dx);
+    if (a->Dy) cudaFree(a->Dy);
+    if (a->fields) cudaFree(a->fields);
+    if (a->dense) cudaFree(a->dense);
+    klb_destroy(a->h);
+    delete a;
+}
+
+klb_t* klb_adjoint_grid(klb_adj_t* a) { return a ? a->h : nullptr; }
+
+int klb_adjoint_forward(klb_adj_t* a, const double* rho, const double* ux, const double* uy, const double* T,
+                        int on_device, double* ke, double* gamma) {
+    if (!a || !rho || !ux || !uy || !T) return a ? afail(a, KLB_E_INVAL, "NULL argument") : KLB_E_INVAL;
+    klb_t* h = a->h;
+    const size_t nn = (size_t)h->g.nx * h->g.ny;
+    const double* src[4] = {rho, ux, uy, T};
+    for (int k = 0; k < 4; ++k)
+        ACK(a, cudaMemcpyAsync(a->fields + k * nn, src[k], nn * sizeof(double),
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+    int r = klb_init_fields(h, a->fields, a->fields + nn, a->fields + 2 * nn, a->fields + 3 * nn, 1);
+    if (r != KLB_OK) return afail(a, r, h->err);
+    for (int s = 0; s < a->nck; ++s) {
+        ACK(a, cudaMemcpyAsync(a->ck[s], h->buf[h->cur], state_bytes(h), cudaMemcpyDeviceToDevice, h->stream));
+        const int64_t n = std::min<int64_t>(a->ckpt, a->nsteps - (int64_t)s * a->ckpt);
+        r = klb_step(h, n);
+        if (r != KLB_OK) return afail(a, r, h->err);
+    }
+    const int64_t M = a->nsteps / h->p.sample_every + 1;
+    std::vector<double> d((size_t)M * 7);
+    int64_t cnt = 0;
+    r = klb_diagnostics(h, d.data(), M, &cnt);
+    if (r != KLB_OK) return afail(a, r, h->err);
+    if (cnt != M) return afail(a, KLB_E_STATE, "unexpected number of samples");
+    a->K.resize(M);
+    for (int64_t s = 0; s < M; ++s) a->K[s] = d[7 * s + 6];
+    a->ke = a->K[M - 1] * h->p.dx * h->p.dy;
+    // gamma: 1/2 OLS slope of ln K over the last 75% of the samples
+    const int start = (int)(M - (3 * M) / 4);
+    const double dts = h->p.dt * h->p.sample_every;
+    double tb = 0, yb = 0;
+    for (int k = start; k < M; ++k) {
+        tb += k * dts;
+        yb += std::log(a->K[k]);
+    }
+    tb /= (M - start);
+    yb /= (M - start);
+    double sxy = 0, sxx = 0;
+    for (int k = start; k < M; ++k) {
+        sxy += (k * dts - tb) * (std::log(a->K[k]) - yb);
+        sxx += (k * dts - tb) * (k * dts - tb);
+    }
+    a->gamma = sxx > 0 ? 0.5 * sxy / sxx : 0.0;
+    if (ke) *ke = a->ke;
+    if (gamma) *gamma = a->gamma;
+    a->forward_done = true;
+    return KLB_OK;
+}
+
+int klb_adjoint_backward(klb_adj_t* a, double g_ke, double g_gamma, double* d_rho, double* d_ux, double* d_uy,
+                         double* d_T, int on_device) {
+    if (!a || !d_rho || !d_ux || !d_uy || !d_T) return a ? afail(a, KLB_E_INVAL, "NULL argument") : KLB_E_INVAL;
+    if (!a->forward_done) return afail(a, KLB_E_STATE, "klb_adjoint_backward before klb_adjoint_forward");
+    klb_t* h = a->h;
+    const bool f64 = h->p.precision == KLB_FP64;
+    // lambda^N = dL/dK_{M-1} dK/df^N, from the final state
+    const int M = (int)a->K.size();
+    int lc = 0;
+    const double cN = dL_dK(a, M - 1, g_ke, g_gamma);
+    int r = f64 ? source<double>(a, h->buf[h->cur], cN, a->lam[lc]) : source<float>(a, h->buf[h->cur], cN, a->lam[lc]);
+    if (r != KLB_OK) return r;
+    r = reverse(a, true, g_ke, g_gamma, &lc);
+    if (r != KLB_OK) return r;
+    // restore the forward grid's final state (the recomputation reused its buffers)
+    const int cur_final = h->cur;
+    (void)cur_final;
+    r = f64 ? fields_grad<double>(a, a->lam[lc], a->dense) : fields_grad<float>(a, a->lam[lc], a->dense);
+    if (r != KLB_OK) return r;
+    const size_t nn = (size_t)h->g.nx * h->g.ny;
+    double* dst[4] = {d_rho, d_ux, d_uy, d_T};
+    for (int k = 0; k < 4; ++k)
+        ACK(a, cudaMemcpyAsync(dst[k], a->dense + k * nn, nn * sizeof(double),
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+    ACK(a, cudaStreamSynchronize(h->stream));
+    a->forward_done = false;  // the forward grid's buffers were reused: run the forward again first
+    return klb_sync(h) == KLB_OK ? KLB_OK : afail(a, KLB_E_CUDA, h->err);
+}
+
+int klb_adjoint_vjp(klb_adj_t* a, const double* lam_N, double* lam_0, int on_device) {
+    if (!a || !lam_N || !lam_0) return a ? afail(a, KLB_E_INVAL, "NULL argument") : KLB_E_INVAL;
+    if (!a->forward_done) return afail(a, KLB_E_STATE, "klb_adjoint_vjp before klb_adjoint_forward");
+    klb_t* h = a->h;
+    const size_t nn = (size_t)h->g.nx * h->g.ny;
+    // lambda^N into the padded layout, through the f import kernel (ghosts unused)
+    ACK(a, cudaMemcpyAsync(a->dense, lam_N, sizeof(double) * NQ * nn,
+                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+    ACK(a, cudaMemsetAsync(a->lam[0], 0, state_bytes(h), h->stream));
+    cudaError_t e = h->p.precision == KLB_FP64 ? launch_set_f<double>(h->g, a->dense, (double*)a->lam[0], h->stream)
+                                                : launch_set_f<float>(h->g, a->dense, (float*)a->lam[0], h->stream);
+    if (e != cudaSuccess) return afail(a, KLB_E_CUDA, cudaGetErrorString(e));
+    int lc = 0;
+    int r = reverse(a, false, 0.0, 0.0, &lc);
+    if (r != KLB_OK) return r;
+    e = h->p.precision == KLB_FP64 ? launch_get_f<double>(h->g, (const double*)a->lam[lc], a->dense, h->stream)
+                                   : launch_get_f<float>(h->g, (const float*)a->lam[lc], a->dense, h->stream);
+    if (e != cudaSuccess) return afail(a, KLB_E_CUDA, cudaGetErrorString(e));
+    ACK(a, cudaMemcpyAsync(lam_0, a->dense, sizeof(double) * NQ * nn,
+                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+    ACK(a, cudaStreamSynchronize(h->stream));
+    a->forward_done = false;
+    return KLB_OK;
+}
+
+int klb_adjoint_samples(klb_adj_t* a, double* out, int64_t cap, int64_t* count) {
+    if (!a || !count || (cap > 0 && !out)) return KLB_E_INVAL;
+    const int64_t m = std::min<int64_t>(cap, (int64_t)a->K.size());
+    for (int64_t s = 0; s < m; ++s) out[s] = a->K[s];
+    *count = m;
+    return KLB_OK;
+}
+
+const char* klb_adjoint_last_error(const klb_adj_t* a) { return a ? a->err.c_str() : g_adj_create_error.c_str(); }
+
+}  // extern "C"

@@ -88,6 +88,15 @@ def lib():
             "klb_batch_launch_count": (i64, [vp]),
             "klb_batch_tiles": (i64, [vp]),
             "klb_batch_last_error": (C.c_char_p, [vp]),
+            "klb_adjoint_create": (C.c_int, [P, i64, C.c_int32, C.POINTER(vp)]),
+            "klb_adjoint_destroy": (None, [vp]),
+            "klb_adjoint_forward": (C.c_int, [vp, vp, vp, vp, vp, C.c_int, C.POINTER(C.c_double),
+                                              C.POINTER(C.c_double)]),
+            "klb_adjoint_backward": (C.c_int, [vp, C.c_double, C.c_double, vp, vp, vp, vp, C.c_int]),
+            "klb_adjoint_vjp": (C.c_int, [vp, vp, vp, C.c_int]),
+            "klb_adjoint_samples": (C.c_int, [vp, vp, i64, C.POINTER(i64)]),
+            "klb_adjoint_grid": (vp, [vp]),
+            "klb_adjoint_last_error": (C.c_char_p, [vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -325,3 +334,83 @@ class KlbBatch:
     @property
     def tiles(self) -> int:
         return int(lib().klb_batch_tiles(self.b))
+
+
+def _acheck(a, code):
+    if code != KLB_OK:
+        msg = lib().klb_adjoint_last_error(a)
+        raise KlbError(code, msg.decode() if msg else "")
+
+
+class KlbAdjoint:
+    """Forward run with checkpoints and its reverse sweep (klb_adjoint_*)."""
+
+    def __init__(self, params: klb_params, nsteps: int, checkpoint_every: int = 45):
+        a = C.c_void_p()
+        code = lib().klb_adjoint_create(C.byref(params), int(nsteps), int(checkpoint_every), C.byref(a))
+        if code != KLB_OK:
+            raise KlbError(code, (lib().klb_adjoint_last_error(None) or b"").decode())
+        self.a = a
+        self.nx, self.ny = params.nx, params.ny
+        self.params = params
+        self.nsteps = nsteps
+        self.grid = Klb(params, _borrowed=lib().klb_adjoint_grid(a))
+
+    @classmethod
+    def from_problem(cls, pb, precision="fp64", checkpoint_every=45, stream=None):
+        p = make_params(pb.nx, pb.ny, pb.dx, pb.dy, pb.dt, pb.tau, v=pb.v, bc_x=pb.bc_x, bc_y=pb.bc_y,
+                        precision=precision, sample_every=pb.sample_every, stream=stream)
+        return cls(p, pb.steps, checkpoint_every)
+
+    def close(self):
+        if getattr(self, "a", None):
+            self.grid.h = None
+            lib().klb_adjoint_destroy(self.a)
+            self.a = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def forward(self, rho, ux, uy, T):
+        ptrs = [_ptr(x) for x in (rho, ux, uy, T)]
+        ond = {p[1] for p in ptrs}
+        if len(ond) != 1:
+            raise TypeError("all four fields must live on the same side (host or device)")
+        ke, gamma = C.c_double(), C.c_double()
+        _acheck(self.a, lib().klb_adjoint_forward(self.a, *[p[0] for p in ptrs], ond.pop(), C.byref(ke),
+                                                  C.byref(gamma)))
+        return ke.value, gamma.value
+
+    def backward(self, g_ke: float, g_gamma: float, out=None):
+        if out is None:
+            out = tuple(np.empty((self.ny, self.nx)) for _ in range(4))
+        ptrs = [_ptr(x) for x in out]
+        ond = {p[1] for p in ptrs}
+        _acheck(self.a, lib().klb_adjoint_backward(self.a, float(g_ke), float(g_gamma), *[p[0] for p in ptrs],
+                                                   ond.pop()))
+        return out
+
+    def vjp(self, lam_N, out=None):
+        if out is None:
+            out = np.empty((19, self.ny, self.nx))
+        pa, da = _ptr(lam_N)
+        pb, db = _ptr(out)
+        if da != db:
+            raise TypeError("lam_N and the output must live on the same side")
+        _acheck(self.a, lib().klb_adjoint_vjp(self.a, pa, pb, da))
+        return out
+
+    def samples(self):
+        out = np.zeros(self.nsteps + 2)
+        cnt = C.c_int64(0)
+        _acheck(self.a, lib().klb_adjoint_samples(self.a, out.ctypes.data, out.size, C.byref(cnt)))
+        return out[: cnt.value].copy()

@@ -1,0 +1,149 @@
+"""The hand-written adjoint of the step (reverse sweep with checkpoints).
+
+Pinned to the oracle: its complex-step run is an exact tangent of the step
+map, so for a random lambda^N and a random perturbation delta of f^0,
+<lambda^N, J delta> (oracle tangent) must equal <J^T lambda^N, delta> (GPU
+adjoint) to rounding; the gradients of KE and gamma with respect to D_v, D_rho
+and the initial u_y field must equal the oracle's complex-step derivatives;
+and central finite differences of the GPU forward (h = 1e-4) must agree to
+their truncation error.
+"""
+import numpy as np
+import pytest
+
+from gpu_common import oracle_params
+from oracle import core, fit
+from paper_1010_4124_gb300 import inputs, klb
+
+pytestmark = pytest.mark.gpu
+
+
+def _small(steps=30, sample_every=5):
+    # a small KHI (thin layers: nonlinear WENO weights active), periodic x, outflow y
+    return inputs.khi(24, 20, steps, Dv=2.0, Drho=3.0, sample_every=sample_every)
+
+
+def _oracle_objective(pb, fields, cs=False):
+    """(KE, gamma) of the oracle run from the fields (complex fields: complex-step)."""
+    p = oracle_params(pb)
+    f0 = core.init_feq(p, *fields, cs=cs)
+    _, d = core.run(p, f0, pb.steps, sample_every=pb.sample_every, cs=cs)
+    K = d[:, 6]
+    ke = K[-1] * pb.dx * pb.dy
+    M = len(K)
+    w = fit.window(M)
+    t = np.arange(M) * pb.sample_every * pb.dt
+    tw = t[w] - t[w].mean()
+    gamma = 0.5 * np.sum(tw * np.log(K[w])) / np.sum(tw**2)
+    return ke, gamma
+
+
+@pytest.mark.parametrize("ckpt", [7, 1, 100])
+def test_dot_product_with_oracle_tangent(ckpt):
+    pb = _small()
+    fields = inputs.fields(pb)
+    p = oracle_params(pb)
+    f0 = core.init_feq(p, *fields)
+    rng = np.random.default_rng(3)
+    delta = rng.standard_normal(f0.shape) * 1e-3
+    lamN = rng.standard_normal(f0.shape)
+    h = 1e-30
+    fN_cs, _ = core.run(p, f0 + 1j * h * delta, pb.steps, cs=True)
+    Jd = np.imag(fN_cs) / h
+    lhs = np.sum(lamN * Jd)
+    with klb.KlbAdjoint.from_problem(pb, "fp64", checkpoint_every=ckpt) as adj:
+        adj.forward(*fields)
+        lam0 = adj.vjp(np.ascontiguousarray(lamN))
+    rhs = np.sum(lam0 * delta)
+    assert rhs == pytest.approx(lhs, rel=1e-10), (lhs, rhs)
+
+
+def test_checkpointing_does_not_change_the_result():
+    pb = _small()
+    fields = inputs.fields(pb)
+    lamN = np.random.default_rng(4).standard_normal((19, pb.ny, pb.nx))
+    out = []
+    for ckpt in (1, 7, 30):
+        with klb.KlbAdjoint.from_problem(pb, "fp64", checkpoint_every=ckpt) as adj:
+            adj.forward(*fields)
+            out.append(adj.vjp(lamN))
+    assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
+
+
+def test_objective_matches_oracle():
+    pb = _small()
+    fields = inputs.fields(pb)
+    ke_ref, g_ref = _oracle_objective(pb, fields)
+    with klb.KlbAdjoint.from_problem(pb, "fp64", checkpoint_every=7) as adj:
+        ke, gamma = adj.forward(*fields)
+    assert ke == pytest.approx(ke_ref, rel=1e-12)
+    assert gamma == pytest.approx(g_ref, rel=1e-10)
+
+
+def test_gradients_match_oracle_complex_step():
+    torch = pytest.importorskip("torch")
+    from paper_1010_4124_gb300.adjoint import khi_loss
+    pb = _small()
+    uy0 = inputs.perturbation_shape(pb)
+    rng = np.random.default_rng(5)
+    dir_uy = rng.standard_normal(uy0.shape)
+    with klb.KlbAdjoint.from_problem(pb, "fp64", checkpoint_every=7) as adj:
+        Dv = torch.tensor(pb.Dv, dtype=torch.float64, requires_grad=True)
+        Dr = torch.tensor(pb.Drho, dtype=torch.float64, requires_grad=True)
+        uy = torch.tensor(uy0, dtype=torch.float64, device="cuda", requires_grad=True)
+        for which in (0, 1):
+            for t in (Dv, Dr, uy):
+                t.grad = None
+            ke, gamma = khi_loss(pb, Dv.cuda(), Dr.cuda(), uy, adj, device="cuda")
+            (ke if which == 0 else gamma).backward()
+            got = [Dv.grad.item(), Dr.grad.item(), float((uy.grad.cpu().numpy() * dir_uy).sum())]
+            h = 1e-25
+            ref = [
+                np.imag(_oracle_objective(pb, inputs.fields(pb, Dv=pb.Dv + 1j * h), cs=True)[which]) / h,
+                np.imag(_oracle_objective(pb, inputs.fields(pb, Drho=pb.Drho + 1j * h), cs=True)[which]) / h,
+                np.imag(_oracle_objective(pb, inputs.fields(pb, uy=uy0 + 1j * h * dir_uy), cs=True)[which]) / h,
+            ]
+            for g, r in zip(got, ref):
+                assert g == pytest.approx(r, rel=1e-8, abs=1e-14 * max(1.0, abs(r))), (which, got, ref)
+
+
+def test_fp32_adjoint_close_to_fp64():
+    pb = _small()
+    fields = inputs.fields(pb)
+    outs = {}
+    for prec in ("fp64", "fp32"):
+        with klb.KlbAdjoint.from_problem(pb, prec, checkpoint_every=7) as adj:
+            adj.forward(*fields)
+            outs[prec] = adj.backward(1.0, 0.0)
+    for a, b in zip(outs["fp32"], outs["fp64"]):
+        scale = np.abs(b).max()
+        assert np.abs(a - b).max() <= 2e-3 * scale
+
+
+def test_config_size_gradient_vs_finite_differences():
+    # 256 x 256 KHI as the single run, 2000 steps, checkpoints every 45:
+    # dKE/dD_v and dKE/dD_rho by the adjoint against central differences of
+    # the GPU forward in FP64 (h = 1e-4)
+    pb = inputs.khi(256, 256, 2000, Dv=4.0, Drho=4.0, sample_every=10)
+    with klb.KlbAdjoint.from_problem(pb, "fp64", checkpoint_every=45) as adj:
+        fields = inputs.fields(pb)
+        adj.forward(*fields)
+        d_rho, d_ux, d_uy, d_T = adj.backward(1.0, 0.0)
+        X, Y = inputs.coords(pb)
+        s = Y / (pb.Dv * pb.dy)
+        dux = 0.5 * pb.u0 / np.cosh(s) ** 2 * (-s / pb.Dv)
+        g_dv = float((d_ux * dux).sum())
+        sr = Y / (pb.Drho * pb.dy)
+        drho = 0.5 * (pb.rho1 - pb.rho2) / np.cosh(sr) ** 2 * (-sr / pb.Drho)
+        rho = fields[0]
+        g_dr = float((d_rho * drho + d_T * (-pb.p0 / rho**2) * drho).sum())
+        h = 1e-4
+        fd = []
+        for key in ("Dv", "Drho"):
+            vals = []
+            for sgn in (1, -1):
+                kw = {key: getattr(pb, key) + sgn * h}
+                vals.append(adj.forward(*inputs.fields(pb, **kw))[0])
+            fd.append((vals[0] - vals[1]) / (2 * h))
+    assert g_dv == pytest.approx(fd[0], rel=1e-5)
+    assert g_dr == pytest.approx(fd[1], rel=1e-5)
