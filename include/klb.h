@@ -271,6 +271,42 @@ int klb_adjoint_samples(klb_adj_t* a, double* out, int64_t cap, int64_t* count);
 klb_t* klb_adjoint_grid(klb_adj_t* a);
 const char* klb_adjoint_last_error(const klb_adj_t* a);
 
+/* Diagnostics of a state without any device allocation (the paper has no
+ * counterpart; this serves callers that cannot allocate device memory while
+ * they run: a host application whose memory manager owns every device
+ * allocation; a service that must not grow its device footprint after
+ * start-up; a latency-bound loop that cannot afford the device-wide
+ * synchronisation a cudaMalloc/cudaFree pair may bring).
+ *
+ * Computes the 7 diagnostics of klb_diagnostics -- sum rho, sum rho u_x,
+ * sum rho u_y, sum rho (T + |u|^2/2), max |u_y|, max rho u_y^2 / 2,
+ * sum rho u_y^2 / 2 over the interior nodes, in FP64 -- of the state f and
+ * writes them to out[0..6], a DEVICE pointer owned by the caller.  f is a
+ * device pointer to plane 0 of a distribution array in the library's layout
+ * (as klb_layout reports it: element (q, j, i) of the interior at
+ * f[q*plane + (j+3)*pitch + (i+4)], in the precision given, KLB_FP32 or
+ * KLB_FP64); v are the ring speeds.  The work is enqueued on `stream` (NULL =
+ * the default stream) and the call returns without waiting; it calls no
+ * cudaMalloc, cudaFree or allocating library routine.  The sums are reduced
+ * in the same order as the handle-based path with kernel variant 0 (the
+ * default), so both agree to the last bit; with variant 1, to rounding.
+ *
+ * Scratch: the per-CTA partial records live in a fixed device array of this
+ * library, 4096 records (256 KiB), held by every GPU that loads the library
+ * until the process exits; FP32 states need one record per CTA (at most two
+ * per SM), FP64 states one per tile of 32 x 8 nodes, so FP64 grids above 4096
+ * tiles are rejected with KLB_E_INVAL and a message.  All calls on a device
+ * share that array and it keeps the last call's contents: calls whose work
+ * overlaps on the GPU (on different streams, or from different threads) race
+ * and must be ordered by the caller.  The first call on each device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  A non-finite state shows as
+ * NaN sums.  Errors: KLB_E_INVAL, KLB_E_CUDA; message:
+ * klb_diagnostics_static_error(). */
+int klb_diagnostics_static(const void* f, int32_t precision, int32_t nx, int32_t ny, int64_t pitch, int64_t plane,
+                           const double v[3], double* out, void* stream);
+const char* klb_diagnostics_static_error(void);
+
 /* Fault injection for tests.  With polls > 0, every later step launch also
  * waits, with a budget of `polls` polls, on a device barrier that nothing
  * arrives on (a flag that nothing sets): the wait runs out, each CTA records

@@ -106,6 +106,8 @@ static void fill_const(const klb_params& p, StepConst<T>& c) {
     c.eps = T(eps);
     c.relax = T(p.dt / p.tau);
 }
+void fdlb::step_constants(const klb_params& p, StepConst<float>& c) { fill_const(p, c); }
+void fdlb::step_constants(const klb_params& p, StepConst<double>& c) { fill_const(p, c); }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,

@@ -45,6 +45,9 @@ struct klb {  // state of one grid
 };
 
 namespace fdlb {
+// the step constants of a problem statement, in either arithmetic type
+void step_constants(const klb_params& p, StepConst<float>& c);
+void step_constants(const klb_params& p, StepConst<double>& c);
 // helpers of klb_capi.cu used by the batch engine
 int handle_fail(klb_t* h, int code, const std::string& msg);
 int handle_upload_descs(klb_t* h);  // (re)build the FP32 descriptors and the tile count

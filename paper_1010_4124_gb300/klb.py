@@ -97,6 +97,8 @@ def lib():
             "klb_adjoint_samples": (C.c_int, [vp, vp, i64, C.POINTER(i64)]),
             "klb_adjoint_grid": (vp, [vp]),
             "klb_adjoint_last_error": (C.c_char_p, [vp]),
+            "klb_diagnostics_static": (C.c_int, [vp, i32, i32, i32, i64, i64, vp, vp, vp]),
+            "klb_diagnostics_static_error": (C.c_char_p, []),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
