@@ -88,16 +88,32 @@ struct ArithF32 {
         for (int k = 0; k < 3; ++k) F[k + 1] = Tm * (c.fk[k][0] + Tm * (c.fk[k][1] + Tm * c.fk[k][2]));
         F[0] = 1.f - 6.f * (F[1] + F[2] + F[3]);
     }
+    // The four collision invariants of g over the 19 velocities: sum g,
+    // sum g v_x, sum g v_y, sum g |v|^2.  Within a ring, direction i + 3 is
+    // -v of direction i (Eq. 5), so each ring contributes through its sum S
+    // (|v|^2 is the ring's) and the three differences of opposite pairs D_i:
+    //   sum g v = sum_{i=1..3} v_i D_i.
+    __device__ __forceinline__ static void invariants(const StepConst<T>& c, const T g[NQ], T& m0, T& mx, T& my,
+                                                      T& me) {
+        m0 = g[0];
+        mx = 0.f;
+        my = 0.f;
+        me = 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int b = 1 + 6 * k;
+            const T D0 = g[b] - g[b + 3], D1 = g[b + 1] - g[b + 4], D2 = g[b + 2] - g[b + 5];
+            const T S = ((g[b] + g[b + 3]) + (g[b + 1] + g[b + 4])) + (g[b + 2] + g[b + 5]);
+            m0 += S;
+            me = fmaf(c.v2[b], S, me);
+            mx = fmaf(c.vx[b], D0, fmaf(c.vx[b + 1], D1, fmaf(c.vx[b + 2], D2, mx)));
+            my = fmaf(c.vy[b], D0, fmaf(c.vy[b + 1], D1, my));  // directions 3 and 6 have v_y = 0
+        }
+    }
     // Eq. (10) with E = sum f |v|^2 / 2 and T = E / rho - |u|^2 / 2.
     __device__ __forceinline__ static NodeEq<T> node_state(const StepConst<T>& c, const T f[NQ]) {
-        T r = 0, jx = 0, jy = 0, e = 0;
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            r += f[q];
-            jx += f[q] * c.vx[q];
-            jy += f[q] * c.vy[q];
-            e += f[q] * c.v2[q];
-        }
+        T r, jx, jy, e;
+        invariants(c, f, r, jx, jy, e);
         const T ir = 1.f / r;
         const T ux = jx * ir, uy = jy * ir;
         return from_moments(c, r, ux, uy, 0.5f * e * ir - 0.5f * (ux * ux + uy * uy));
@@ -119,11 +135,17 @@ struct ArithF32 {
         for (int k = 0; k < 4; ++k) s.rF[k] = r * F[k];
         return s;
     }
-    // Eq. (28): f^(0) = rho F_k [A + A w + w^2/2 + w^3/6], w = v.u/T.
+    // Eq. (28): f^(0) = rho F_k [A + A w + w^2/2 + w^3/6], w = v.u/T, written
+    // as E + O with E = A + w^2/2 and O = w (A + w^2/6); direction i + 3 of a
+    // ring has -w, hence E - O (the same operations as collide()).
     __device__ __forceinline__ static T feq(const StepConst<T>& c, const NodeEq<T>& s, int q) {
-        const T w = c.vx[q] * s.a + c.vy[q] * s.b;
-        const T br = s.A + s.A * w + w * w * (0.5f + w * (1.f / 6.f));
-        return s.rF[ring_of(q)] * br;
+        if (q == 0) return s.rF[0] * s.A;
+        const int k = (q - 1) / 6, i = (q - 1) % 6, ib = i % 3, b = 1 + 6 * k;
+        const T w = ib < 2 ? fmaf(c.vy[b + ib], s.b, c.vx[b + ib] * s.a) : c.vx[b + ib] * s.a;
+        const T w2 = w * w;
+        const T E = fmaf(0.5f, w2, s.A);
+        const T O = w * fmaf(w2, 1.f / 6.f, s.A);
+        return s.rF[k + 1] * (i < 3 ? E + O : E - O);
     }
     // WENO5 flux on the unscaled plane (eps already divided by v^2), over a
     // common denominator: h = c + sum delta_q g_q P_q / sum delta_q P_q with
@@ -193,25 +215,45 @@ struct ArithF32 {
     // residual is projected out: d' = d - B^T (B B^T)^{-1} B d with
     // B = (1, v_x, v_y, |v|^2).  The projection changes nothing in exact
     // arithmetic and keeps the collision conservative to the rounding of d.
+    //
+    // f^(0) is evaluated per opposite pair: with w = v.u/T for direction i,
+    // direction i + 3 has -w, and the bracket splits into an even part
+    // E = A + w^2/2 and an odd part O = w (A + w^2/6): br(+-w) = E +- O.
     __device__ __forceinline__ static void collide(const StepConst<T>& c, const NodeEq<T>& s, T f[NQ]) {
         T d[NQ];
-        T m0 = 0, mx = 0, my = 0, me = 0;
+        d[0] = f[0] - s.rF[0] * s.A;
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            d[q] = f[q] - feq(c, s, q);
-            m0 += d[q];
-            mx += d[q] * c.vx[q];
-            my += d[q] * c.vy[q];
-            me += d[q] * c.v2[q];
+        for (int k = 0; k < 3; ++k) {
+            const int b = 1 + 6 * k;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const T w = i < 2 ? fmaf(c.vy[b + i], s.b, c.vx[b + i] * s.a) : c.vx[b + i] * s.a;
+                const T w2 = w * w;
+                const T E = fmaf(0.5f, w2, s.A);
+                const T O = w * fmaf(w2, 1.f / 6.f, s.A);
+                d[b + i] = f[b + i] - s.rF[k + 1] * (E + O);
+                d[b + i + 3] = f[b + i + 3] - s.rF[k + 1] * (E - O);
+            }
         }
+        T m0, mx, my, me;
+        invariants(c, d, m0, mx, my, me);
         T lam[4];
 #pragma unroll
         for (int a = 0; a < 4; ++a)
             lam[a] = c.ginv[a][0] * m0 + c.ginv[a][1] * mx + c.ginv[a][2] * my + c.ginv[a][3] * me;
+        // the projection B^T lam of velocity q: lam_0 + lam_3 |v|^2 + lam_x v_x + lam_y v_y,
+        // the last two odd under v -> -v
+        f[0] = fmaf(-c.relax, d[0] - lam[0], f[0]);
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            const T dq = d[q] - (lam[0] + lam[1] * c.vx[q] + lam[2] * c.vy[q] + lam[3] * c.v2[q]);
-            f[q] = f[q] - c.relax * dq;
+        for (int k = 0; k < 3; ++k) {
+            const int b = 1 + 6 * k;
+            const T even = fmaf(lam[3], c.v2[b], lam[0]);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const T odd = i < 2 ? fmaf(lam[2], c.vy[b + i], lam[1] * c.vx[b + i]) : lam[1] * c.vx[b + i];
+                f[b + i] = fmaf(-c.relax, (d[b + i] - even) - odd, f[b + i]);
+                f[b + i + 3] = fmaf(-c.relax, (d[b + i + 3] - even) + odd, f[b + i + 3]);
+            }
         }
     }
 };

@@ -17,7 +17,9 @@
 //  * y fluxes: each thread evaluates the face BELOW its node and leaves it in
 //    shared memory; the faces above the tile's top row are evaluated by 12
 //    warps (one velocity each); after one barrier each node reads the face
-//    above it from its upper neighbour.
+//    above it from its upper neighbour.  That barrier is the only one per
+//    tile with 16-row tiles (two face buffers, used by alternate tiles); the
+//    8-row tiles (two CTAs per SM, one face buffer) add one at the tile's end.
 //  * Per node: moments, F_k, f^(0) and the conservative BGK relaxation
 //    (ArithF32::collide) in registers, the flux divergence, and a coalesced
 //    store; nodes next to a periodic or outflow side also write their ghost
@@ -42,7 +44,10 @@ struct Shape {
     static constexpr int BOX_FLOATS = NQ * PLANE;
     static constexpr int BUF_FLOATS = (BOX_FLOATS + 31) / 32 * 32;  // 128-byte multiple (TMA destination)
     static constexpr int YF_FLOATS = NYV * (TY + 1) * 32;
-    static constexpr size_t SMEM_BYTES = sizeof(float) * (2 * BUF_FLOATS + YF_FLOATS) + 128;
+    // face buffers: two (alternating tiles) when one CTA holds the SM, so that
+    // no barrier is needed at the end of a tile; one when two CTAs share it
+    static constexpr int YB = TY == 16 ? 2 : 1;
+    static constexpr size_t SMEM_BYTES = sizeof(float) * (2 * BUF_FLOATS + YB * YF_FLOATS) + 128;
     static_assert((sizeof(float) * BUF_FLOATS) % 128 == 0, "TMA destination must stay 128-byte aligned");
 };
 }  // namespace v3
@@ -182,7 +187,7 @@ __global__ void __launch_bounds__(32 * TY, 16 / TY) step_f32_kernel(const __grid
     // 128-byte boundary of the shared window whatever precedes them
     float* buf = reinterpret_cast<float*>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
     using S = v3::Shape<TY>;
-    float* yf = buf + 2 * S::BUF_FLOATS;
+    float* const yf0 = buf + 2 * S::BUF_FLOATS;
     __shared__ __align__(8) uint64_t full[2];
     __shared__ __align__(8) uint64_t never;  // fault injection: a barrier nothing arrives on
     __shared__ int first[kMaxInstances];
@@ -213,25 +218,18 @@ __global__ void __launch_bounds__(32 * TY, 16 / TY) step_f32_kernel(const __grid
     int k = 0;  // local tile counter: buffer k & 1, phase (k >> 1) & 1
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
         const int b = k & 1;
-        // prefetch the next tile into the other buffer (freed by the barrier
-        // that closed the previous tile)
+        // prefetch the next tile into the other buffer (last read before the
+        // middle barrier of the previous tile)
         if (tid == 0 && t + (int)gridDim.x < ntiles) {
             fence_proxy_async();
             issue(t + gridDim.x, b ^ 1);
         }
+        // A wait that gives up is reported at the barrier in the middle of
+        // the tile; until then the thread computes on whatever the buffer
+        // holds (shared-memory reads only) and stores nothing.
         bool late = !mbar_wait_bounded(smem_u32(&full[b]), (k >> 1) & 1, spin_limit);
         if (inject) late = late || !mbar_wait_bounded(smem_u32(&never), 0, spin_limit);
-        if (__syncthreads_or(late)) {
-            if (tid == 0) {
-                atomicOr(err, ERR_TIMEOUT);
-                // let both copies that may be in flight land before leaving
-                mbar_wait_bounded(smem_u32(&full[b]), (k >> 1) & 1, kDrainPolls);
-                if (t + (int)gridDim.x < ntiles)
-                    mbar_wait_bounded(smem_u32(&full[b ^ 1]), ((k + 1) >> 1) & 1, kDrainPolls);
-            }
-            __syncthreads();
-            return;
-        }
+        float* yf = yf0 + (S::YB == 2 ? b : 0) * S::YF_FLOATS;
         const InstDesc* D = descs + find_inst(first, ninst, t);
         const Geom g = D->g;
         float* __restrict__ out = D->out;
@@ -271,7 +269,19 @@ __global__ void __launch_bounds__(32 * TY, 16 / TY) step_f32_kernel(const __grid
         pass_a_xx<TY, 9, 12>(c, tile, r, s, f);
         pass_a_xx<TY, 15, 18>(c, tile, r, s, f);
         top_faces<TY, 0>(c, tile, yf, s, lane, ty);  // faces above the tile's top row
-        __syncthreads();
+        // All faces are in shared memory and nobody reads this tile buffer
+        // again (the next copy into it is issued after this barrier).
+        if (__syncthreads_or(late)) {
+            if (tid == 0) {
+                atomicOr(err, ERR_TIMEOUT);
+                // let both copies that may be in flight land before leaving
+                mbar_wait_bounded(smem_u32(&full[b]), (k >> 1) & 1, kDrainPolls);
+                if (t + (int)gridDim.x < ntiles)
+                    mbar_wait_bounded(smem_u32(&full[b ^ 1]), ((k + 1) >> 1) & 1, kDrainPolls);
+            }
+            __syncthreads();
+            return;
+        }
         // y fluxes from the faces below and above each node
 #pragma unroll
         for (int q = 1; q < NQ; ++q) {
@@ -289,7 +299,10 @@ __global__ void __launch_bounds__(32 * TY, 16 / TY) step_f32_kernel(const __grid
                 for (int q = 0; q < NQ; ++q) write_images(out, g, q, ix, iy, f[q]);
             }
         }
-        __syncthreads();  // the tile buffer and the face buffer are free again
+        // With two face buffers, the next tile writes the other one, and the
+        // one read here is written again only after every thread has passed
+        // the next tile's middle barrier.  With one, wait for all readers.
+        if (S::YB == 1) __syncthreads();
     }
     if (diag) diag_block_reduce<S::NT>(dv, diag_partials + 8ll * blockIdx.x);
 }
