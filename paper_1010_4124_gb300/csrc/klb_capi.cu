@@ -51,9 +51,9 @@ static void fill_const(const klb_params& p, StepConst<T>& c) {
         c.v2[q] = T(vx * vx + vy * vy);
         c.cx[q] = T(p.dt * vx / p.dx);
         c.cy[q] = T(p.dt * vy / p.dy);
-        // FP32 weno() works with 3 sigma, hence 3 eps; the FP64 path uses eps itself
-        c.ex[q] = vx != 0 ? T(3.0 * eps / (vx * vx)) : T(0);
-        c.ey[q] = vy != 0 ? T(3.0 * eps / (vy * vy)) : T(0);
+        // FP32 weno() works with sigma scaled by 3/4, hence eps too; the FP64 path uses eps itself
+        c.ex[q] = vx != 0 ? T(0.75 * eps / (vx * vx)) : T(0);
+        c.ey[q] = vy != 0 ? T(0.75 * eps / (vy * vy)) : T(0);
     }
     // F_k(T) = T [a_{k+1} a_{k+2} - 4 (a_{k+1} + a_{k+2}) T + 24 T^2] / [3 a_k (a_k - a_{k+1})(a_k - a_{k+2})]
     for (int k = 0; k < 3; ++k) {

@@ -42,7 +42,7 @@ struct StepConst {
     T v2[NQ];          // |v_q|^2
     // FP32 path
     T cx[NQ], cy[NQ];  // dt * v_qx / dx, dt * v_qy / dy
-    T ex[NQ], ey[NQ];  // FP32 WENO: 3 eps / v_qx^2, 3 eps / v_qy^2 (unscaled plane, 3 sigma)
+    T ex[NQ], ey[NQ];  // FP32 WENO: (3/4) eps / v_qx^2, (3/4) eps / v_qy^2 (unscaled plane, sigma scaled by 3/4)
     T fk[3][3];        // F_k(T) = T (fk[k][0] + T (fk[k][1] + T fk[k][2])), k = 1..3
     T ginv[4][4];      // inverse Gram matrix of the collision invariants (1, v_x, v_y, |v|^2)
     // FP64 path (the paper's formulas term by term)
@@ -76,7 +76,10 @@ __device__ __forceinline__ float rcp_approx(float x) {
 }
 
 // ===========================================================================
-// FP32 production arithmetic.
+// FP32 production arithmetic.  Every operation is written as an explicitly
+// rounded multiply, add or fused multiply-add, so that the compiler cannot
+// contract differently in different kernels: every kernel that evaluates a
+// node (either tile shape of the step, the diagnostics) gets the same bits.
 // ===========================================================================
 struct ArithF32 {
     using T = float;
@@ -85,8 +88,8 @@ struct ArithF32 {
     // F_0 = 1 - 6 (F_1 + F_2 + F_3).
     __device__ __forceinline__ static void global_coeffs(const StepConst<T>& c, T Tm, T F[4]) {
 #pragma unroll
-        for (int k = 0; k < 3; ++k) F[k + 1] = Tm * (c.fk[k][0] + Tm * (c.fk[k][1] + Tm * c.fk[k][2]));
-        F[0] = 1.f - 6.f * (F[1] + F[2] + F[3]);
+        for (int k = 0; k < 3; ++k) F[k + 1] = __fmul_rn(Tm, fmaf(Tm, fmaf(Tm, c.fk[k][2], c.fk[k][1]), c.fk[k][0]));
+        F[0] = fmaf(-6.f, __fadd_rn(__fadd_rn(F[1], F[2]), F[3]), 1.f);
     }
     // The four collision invariants of g over the 19 velocities: sum g,
     // sum g v_x, sum g v_y, sum g |v|^2.  Within a ring, direction i + 3 is
@@ -102,9 +105,11 @@ struct ArithF32 {
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const int b = 1 + 6 * k;
-            const T D0 = g[b] - g[b + 3], D1 = g[b + 1] - g[b + 4], D2 = g[b + 2] - g[b + 5];
-            const T S = ((g[b] + g[b + 3]) + (g[b + 1] + g[b + 4])) + (g[b + 2] + g[b + 5]);
-            m0 += S;
+            const T D0 = __fsub_rn(g[b], g[b + 3]), D1 = __fsub_rn(g[b + 1], g[b + 4]);
+            const T D2 = __fsub_rn(g[b + 2], g[b + 5]);
+            const T S = __fadd_rn(__fadd_rn(__fadd_rn(g[b], g[b + 3]), __fadd_rn(g[b + 1], g[b + 4])),
+                                  __fadd_rn(g[b + 2], g[b + 5]));
+            m0 = __fadd_rn(m0, S);
             me = fmaf(c.v2[b], S, me);
             mx = fmaf(c.vx[b], D0, fmaf(c.vx[b + 1], D1, fmaf(c.vx[b + 2], D2, mx)));
             my = fmaf(c.vy[b], D0, fmaf(c.vy[b + 1], D1, my));  // directions 3 and 6 have v_y = 0
@@ -114,9 +119,10 @@ struct ArithF32 {
     __device__ __forceinline__ static NodeEq<T> node_state(const StepConst<T>& c, const T f[NQ]) {
         T r, jx, jy, e;
         invariants(c, f, r, jx, jy, e);
-        const T ir = 1.f / r;
-        const T ux = jx * ir, uy = jy * ir;
-        return from_moments(c, r, ux, uy, 0.5f * e * ir - 0.5f * (ux * ux + uy * uy));
+        const T ir = rcp_approx(r);
+        const T ux = __fmul_rn(jx, ir), uy = __fmul_rn(jy, ir);
+        const T u2 = fmaf(ux, ux, __fmul_rn(uy, uy));
+        return from_moments(c, r, ux, uy, fmaf(__fmul_rn(0.5f, e), ir, __fmul_rn(-0.5f, u2)));
     }
     __device__ __forceinline__ static NodeEq<T> from_moments(const StepConst<T>& c, T r, T ux, T uy, T Tm) {
         NodeEq<T> s;
@@ -124,28 +130,28 @@ struct ArithF32 {
         s.ux = ux;
         s.uy = uy;
         s.Tm = Tm;
-        const T u2 = ux * ux + uy * uy;
-        const T iT = 1.f / Tm;
-        s.A = 1.f - 0.5f * u2 * iT;
-        s.a = ux * iT;
-        s.b = uy * iT;
+        const T u2 = fmaf(ux, ux, __fmul_rn(uy, uy));
+        const T iT = rcp_approx(Tm);
+        s.A = fmaf(__fmul_rn(-0.5f, u2), iT, 1.f);
+        s.a = __fmul_rn(ux, iT);
+        s.b = __fmul_rn(uy, iT);
         T F[4];
         global_coeffs(c, Tm, F);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) s.rF[k] = r * F[k];
+        for (int k = 0; k < 4; ++k) s.rF[k] = __fmul_rn(r, F[k]);
         return s;
     }
     // Eq. (28): f^(0) = rho F_k [A + A w + w^2/2 + w^3/6], w = v.u/T, written
     // as E + O with E = A + w^2/2 and O = w (A + w^2/6); direction i + 3 of a
     // ring has -w, hence E - O (the same operations as collide()).
     __device__ __forceinline__ static T feq(const StepConst<T>& c, const NodeEq<T>& s, int q) {
-        if (q == 0) return s.rF[0] * s.A;
+        if (q == 0) return __fmul_rn(s.rF[0], s.A);
         const int k = (q - 1) / 6, i = (q - 1) % 6, ib = i % 3, b = 1 + 6 * k;
-        const T w = ib < 2 ? fmaf(c.vy[b + ib], s.b, c.vx[b + ib] * s.a) : c.vx[b + ib] * s.a;
-        const T w2 = w * w;
+        const T w = ib < 2 ? fmaf(c.vy[b + ib], s.b, __fmul_rn(c.vx[b + ib], s.a)) : __fmul_rn(c.vx[b + ib], s.a);
+        const T w2 = __fmul_rn(w, w);
         const T E = fmaf(0.5f, w2, s.A);
-        const T O = w * fmaf(w2, 1.f / 6.f, s.A);
-        return s.rF[k + 1] * (i < 3 ? E + O : E - O);
+        const T O = __fmul_rn(w, fmaf(w2, 1.f / 6.f, s.A));
+        return __fmul_rn(s.rF[k + 1], i < 3 ? __fadd_rn(E, O) : __fsub_rn(E, O));
     }
     // WENO5 flux on the unscaled plane (eps already divided by v^2), over a
     // common denominator: h = c + sum delta_q g_q P_q / sum delta_q P_q with
@@ -153,26 +159,26 @@ struct ArithF32 {
     // (eps + sigma)^2 (Eqs. 52-55); one reciprocal instead of four divisions.
     // Since every term scales with v except the absolute epsilon,
     // h(v f; eps) = v h(f; eps / v^2): the factor v sits in the update.
-    __device__ __forceinline__ static T weno(T a, T b, T c, T d, T e, T eps3) {
-        // differences of neighbouring values; in them the smoothness
-        // indicators of Eqs. (53)-(55) read
-        //   3 sigma_1 = 4 D1^2 - 11 D1 D2 + 10 D2^2,
-        //   3 sigma_2 = 4 D2^2 -  5 D2 D3 +  4 D3^2,
-        //   3 sigma_3 = 10 D3^2 - 11 D3 D4 + 4 D4^2,
-        // and the candidates of Eqs. (49)-(51) relative to c read
-        //   h_1 - c = (5 D2 - 2 D1)/6, h_2 - c = (D2 + 2 D3)/6, h_3 - c = (4 D3 - D4)/6.
-        // The weights use 3 sigma and 3 eps (eps3): the common factor cancels.
-        // With e4 = d - e = -D4 (no negation needed) and the optimal weights and
-        // the 1/6 of the candidates folded into the differences,
-        //   h = c + sum_q (delta_q / 6) G_q P_q / sum_q delta_q P_q.
+    __device__ __forceinline__ static T weno(T a, T b, T c, T d, T e, T eps) {
+        // With the differences of neighbouring values D1 = b - a, D2 = c - b,
+        // D3 = d - c and e4 = d - e, the smoothness indicators of
+        // Eqs. (53)-(55), scaled by 3/4, read
+        //   s_1 = D1 (D1 - 11/4 D2) + 5/2 D2^2,
+        //   s_2 = D2 (D2 - 5/4 D3) + D3^2,
+        //   s_3 = e4 (e4 + 11/4 D3) + 5/2 D3^2,
+        // and eps (the constant passed in) is scaled by 3/4 as well: the
+        // common factor cancels in the weights.  The candidates of Eqs. (49)-(51)
+        // relative to c read h_1 - c = (5 D2 - 2 D1)/6, h_2 - c = (D2 + 2 D3)/6,
+        // h_3 - c = (4 D3 + e4)/6; with the optimal weights delta_q and the 1/6
+        // folded in, h = c + sum_q G_q P_q / sum_q delta_q P_q.
         // Every operation is an explicitly rounded multiply, add or fused
         // multiply-add, in the same order as each lane of weno2(), so the
         // scalar and packed evaluations give the same bits.
         const T d1 = fmaf(a, -1.f, b), d2 = fmaf(b, -1.f, c), d3 = fmaf(c, -1.f, d), e4 = fmaf(e, -1.f, d);
         const T a2 = __fmul_rn(d2, d2), a3 = __fmul_rn(d3, d3);
-        const T s1 = fmaf(d1, fmaf(4.f, d1, __fmul_rn(-11.f, d2)), fmaf(10.f, a2, eps3));
-        const T s2 = fmaf(4.f, __fadd_rn(a2, a3), fmaf(__fmul_rn(-5.f, d2), d3, eps3));
-        const T s3 = fmaf(e4, fmaf(4.f, e4, __fmul_rn(11.f, d3)), fmaf(10.f, a3, eps3));
+        const T s1 = fmaf(d1, fmaf(-2.75f, d2, d1), fmaf(2.5f, a2, eps));
+        const T s2 = fmaf(d2, fmaf(-1.25f, d3, d2), fmaf(d3, d3, eps));
+        const T s3 = fmaf(e4, fmaf(2.75f, d3, e4), fmaf(2.5f, a3, eps));
         const T p1 = __fmul_rn(s1, s1), p2 = __fmul_rn(s2, s2), p3 = __fmul_rn(s3, s3);
         const T P23 = __fmul_rn(p2, p3), P13 = __fmul_rn(p1, p3), P12 = __fmul_rn(p1, p2);
         const T G1 = fmaf(0.5f / 6.f, d2, __fmul_rn(-0.2f / 6.f, d1));
@@ -184,21 +190,19 @@ struct ArithF32 {
     }
     // The same flux for two independent faces at once (packed f32x2
     // arithmetic: one instruction for both lanes of the pair).
-    __device__ __forceinline__ static float2 weno2(float2 a, float2 b, float2 c, float2 d, float2 e, float2 eps3) {
+    __device__ __forceinline__ static float2 weno2(float2 a, float2 b, float2 c, float2 d, float2 e, float2 eps) {
         // lane by lane the same operations as weno()
         const float2 m1 = make_float2(-1.f, -1.f);
         const float2 d1 = __ffma2_rn(a, m1, b), d2 = __ffma2_rn(b, m1, c);
         const float2 d3 = __ffma2_rn(c, m1, d), e4 = __ffma2_rn(e, m1, d);
         const float2 a2 = __fmul2_rn(d2, d2), a3 = __fmul2_rn(d3, d3);
-        const float2 k4 = make_float2(4.f, 4.f), k10 = make_float2(10.f, 10.f);
-        const float2 s1 = __ffma2_rn(d1, __ffma2_rn(k4, d1, __fmul2_rn(make_float2(-11.f, -11.f), d2)),
-                                     __ffma2_rn(k10, a2, eps3));
-        const float2 s2 = __ffma2_rn(k4, __fadd2_rn(a2, a3), __ffma2_rn(__fmul2_rn(make_float2(-5.f, -5.f), d2), d3, eps3));
-        const float2 s3 = __ffma2_rn(e4, __ffma2_rn(k4, e4, __fmul2_rn(make_float2(11.f, 11.f), d3)),
-                                     __ffma2_rn(k10, a3, eps3));
+        const float2 k25 = make_float2(2.5f, 2.5f);
+        const float2 s1 = __ffma2_rn(d1, __ffma2_rn(make_float2(-2.75f, -2.75f), d2, d1), __ffma2_rn(k25, a2, eps));
+        const float2 s2 = __ffma2_rn(d2, __ffma2_rn(make_float2(-1.25f, -1.25f), d3, d2), __ffma2_rn(d3, d3, eps));
+        const float2 s3 = __ffma2_rn(e4, __ffma2_rn(make_float2(2.75f, 2.75f), d3, e4), __ffma2_rn(k25, a3, eps));
         const float2 p1 = __fmul2_rn(s1, s1), p2 = __fmul2_rn(s2, s2), p3 = __fmul2_rn(s3, s3);
         const float2 P23 = __fmul2_rn(p2, p3), P13 = __fmul2_rn(p1, p3), P12 = __fmul2_rn(p1, p2);
-        // (delta_1/6)(5 D2 - 2 D1), (delta_2/6)(D2 + 2 D3), (delta_3/6)(4 D3 - D4)
+        // (delta_1/6)(5 D2 - 2 D1), (delta_2/6)(D2 + 2 D3), (delta_3/6)(4 D3 + e4)
         const float2 G1 = __ffma2_rn(make_float2(0.5f / 6.f, 0.5f / 6.f), d2, __fmul2_rn(make_float2(-0.2f / 6.f, -0.2f / 6.f), d1));
         const float2 G2 = __ffma2_rn(make_float2(1.2f / 6.f, 1.2f / 6.f), d3, __fmul2_rn(make_float2(0.1f, 0.1f), d2));
         const float2 G3 = __ffma2_rn(make_float2(1.2f / 6.f, 1.2f / 6.f), d3, __fmul2_rn(make_float2(0.05f, 0.05f), e4));
@@ -221,18 +225,18 @@ struct ArithF32 {
     // E = A + w^2/2 and an odd part O = w (A + w^2/6): br(+-w) = E +- O.
     __device__ __forceinline__ static void collide(const StepConst<T>& c, const NodeEq<T>& s, T f[NQ]) {
         T d[NQ];
-        d[0] = f[0] - s.rF[0] * s.A;
+        d[0] = fmaf(-s.rF[0], s.A, f[0]);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const int b = 1 + 6 * k;
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
-                const T w = i < 2 ? fmaf(c.vy[b + i], s.b, c.vx[b + i] * s.a) : c.vx[b + i] * s.a;
-                const T w2 = w * w;
+                const T w = i < 2 ? fmaf(c.vy[b + i], s.b, __fmul_rn(c.vx[b + i], s.a)) : __fmul_rn(c.vx[b + i], s.a);
+                const T w2 = __fmul_rn(w, w);
                 const T E = fmaf(0.5f, w2, s.A);
-                const T O = w * fmaf(w2, 1.f / 6.f, s.A);
-                d[b + i] = f[b + i] - s.rF[k + 1] * (E + O);
-                d[b + i + 3] = f[b + i + 3] - s.rF[k + 1] * (E - O);
+                const T O = __fmul_rn(w, fmaf(w2, 1.f / 6.f, s.A));
+                d[b + i] = fmaf(-s.rF[k + 1], __fadd_rn(E, O), f[b + i]);
+                d[b + i + 3] = fmaf(-s.rF[k + 1], __fsub_rn(E, O), f[b + i + 3]);
             }
         }
         T m0, mx, my, me;
@@ -240,19 +244,20 @@ struct ArithF32 {
         T lam[4];
 #pragma unroll
         for (int a = 0; a < 4; ++a)
-            lam[a] = c.ginv[a][0] * m0 + c.ginv[a][1] * mx + c.ginv[a][2] * my + c.ginv[a][3] * me;
+            lam[a] = fmaf(c.ginv[a][3], me, fmaf(c.ginv[a][2], my, fmaf(c.ginv[a][1], mx, __fmul_rn(c.ginv[a][0], m0))));
         // the projection B^T lam of velocity q: lam_0 + lam_3 |v|^2 + lam_x v_x + lam_y v_y,
         // the last two odd under v -> -v
-        f[0] = fmaf(-c.relax, d[0] - lam[0], f[0]);
+        f[0] = fmaf(-c.relax, __fsub_rn(d[0], lam[0]), f[0]);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const int b = 1 + 6 * k;
             const T even = fmaf(lam[3], c.v2[b], lam[0]);
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
-                const T odd = i < 2 ? fmaf(lam[2], c.vy[b + i], lam[1] * c.vx[b + i]) : lam[1] * c.vx[b + i];
-                f[b + i] = fmaf(-c.relax, (d[b + i] - even) - odd, f[b + i]);
-                f[b + i + 3] = fmaf(-c.relax, (d[b + i + 3] - even) + odd, f[b + i + 3]);
+                const T odd = i < 2 ? fmaf(lam[2], c.vy[b + i], __fmul_rn(lam[1], c.vx[b + i]))
+                                    : __fmul_rn(lam[1], c.vx[b + i]);
+                f[b + i] = fmaf(-c.relax, __fsub_rn(__fsub_rn(d[b + i], even), odd), f[b + i]);
+                f[b + i + 3] = fmaf(-c.relax, __fadd_rn(__fsub_rn(d[b + i + 3], even), odd), f[b + i + 3]);
             }
         }
     }
@@ -426,13 +431,14 @@ __device__ __forceinline__ void write_images(T* __restrict__ out, const Geom& g,
 template <typename T>
 __device__ __forceinline__ void node_diag(const NodeEq<T>& s, bool active, double v[8]) {
     if (active) {
+        // explicitly rounded operations: the same bits in every kernel that calls this
         double r = s.rho, u = s.ux, w = s.uy, Tm = s.Tm;
         v[0] = r;
-        v[1] = r * u;
-        v[2] = r * w;
-        v[3] = r * (Tm + 0.5 * (u * u + w * w));
+        v[1] = __dmul_rn(r, u);
+        v[2] = __dmul_rn(r, w);
+        v[3] = __dmul_rn(r, __dadd_rn(Tm, __dmul_rn(0.5, __dadd_rn(__dmul_rn(u, u), __dmul_rn(w, w)))));
         v[4] = fabs(w);
-        v[5] = 0.5 * r * w * w;
+        v[5] = __dmul_rn(__dmul_rn(__dmul_rn(0.5, r), w), w);
         v[6] = v[5];
         v[7] = (r > 0.0 && Tm > 0.0) ? 0.0 : 1.0;  // also catches NaN
     } else {

@@ -109,7 +109,7 @@ __device__ __forceinline__ void pass_a_xy(const StepConst<float>& c, const float
     yst<SGY>(P, r, s, w);
     const float2 h = weno_pair(u, w, c.ex[Q], c.ey[Q]);
     const float hr = __shfl_down_sync(0xffffffffu, h.x, 1);
-    post[Q] -= c.cx[Q] * (hr - h.x);
+    post[Q] = fmaf(-c.cx[Q], __fsub_rn(hr, h.x), post[Q]);
     yf[(yslot(Q) * (TY + 1) + ty) * 32 + lane] = h.y;
 }
 // pass A for two velocities QA, QB with an x component only
@@ -122,26 +122,31 @@ __device__ __forceinline__ void pass_a_xx(const StepConst<float>& c, const float
     const float2 h = weno_pair(u, w, c.ex[QA], c.ex[QB]);
     const float ra = __shfl_down_sync(0xffffffffu, h.x, 1);
     const float rb = __shfl_down_sync(0xffffffffu, h.y, 1);
-    post[QA] -= c.cx[QA] * (ra - h.x);
-    post[QB] -= c.cx[QB] * (rb - h.y);
+    post[QA] = fmaf(-c.cx[QA], __fsub_rn(ra, h.x), post[QA]);
+    post[QB] = fmaf(-c.cx[QB], __fsub_rn(rb, h.y), post[QB]);
 }
 
-// the faces above the tile's top row, velocity of y slot K, for lane's column
+// the faces above the tile's top row, velocities of y slots K and K + 1 (one
+// packed evaluation), for lane's column
 template <int TY, int K>
-__device__ __forceinline__ void top_face(const StepConst<float>& c, const float* tile, float* yf, int s, int lane) {
-    constexpr int Q = yvel(K);
-    constexpr int SGY = sgn_y(Q);
-    float u[5];
-    yst<SGY>(tile + Q * v3::Shape<TY>::PLANE, TY + 3, s, u);
-    yf[(K * (TY + 1) + TY) * 32 + lane] = ArithF32::weno(u[0], u[1], u[2], u[3], u[4], c.ey[Q]);
+__device__ __forceinline__ void top_face_pair(const StepConst<float>& c, const float* tile, float* yf, int s,
+                                              int lane) {
+    constexpr int QA = yvel(K), QB = yvel(K + 1);
+    float u[5], w[5];
+    yst<sgn_y(QA)>(tile + QA * v3::Shape<TY>::PLANE, TY + 3, s, u);
+    yst<sgn_y(QB)>(tile + QB * v3::Shape<TY>::PLANE, TY + 3, s, w);
+    const float2 h = weno_pair(u, w, c.ey[QA], c.ey[QB]);
+    yf[(K * (TY + 1) + TY) * 32 + lane] = h.x;
+    yf[((K + 1) * (TY + 1) + TY) * 32 + lane] = h.y;
 }
-// warp w evaluates the top faces of y slots w, w + TY, ... (12 slots)
+// warp w < 6 evaluates the top faces of y slots 2w and 2w + 1
 template <int TY, int K>
 __device__ __forceinline__ void top_faces(const StepConst<float>& c, const float* tile, float* yf, int s, int lane,
                                           int w) {
+    static_assert(v3::NYV % 2 == 0 && v3::NYV / 2 <= TY, "one slot pair per warp");
     if constexpr (K < v3::NYV) {
-        if (w == K % TY) top_face<TY, K>(c, tile, yf, s, lane);
-        top_faces<TY, K + 1>(c, tile, yf, s, lane, w);
+        if (w == K / 2) top_face_pair<TY, K>(c, tile, yf, s, lane);
+        top_faces<TY, K + 2>(c, tile, yf, s, lane, w);
     }
 }
 
@@ -215,6 +220,11 @@ __global__ void __launch_bounds__(32 * TY, 16 / TY) step_f32_kernel(const __grid
 
     double dv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     const bool diag = diag_partials != nullptr;
+    // fields of the instance of the current tile, read from global memory
+    // only when the instance changes (tiles of one instance are contiguous)
+    int cur = -1, first_t = 0, tiles_x = 1;
+    Geom g{};
+    float* out = nullptr;
     int k = 0;  // local tile counter: buffer k & 1, phase (k >> 1) & 1
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
         const int b = k & 1;
@@ -230,11 +240,17 @@ __global__ void __launch_bounds__(32 * TY, 16 / TY) step_f32_kernel(const __grid
         bool late = !mbar_wait_bounded(smem_u32(&full[b]), (k >> 1) & 1, spin_limit);
         if (inject) late = late || !mbar_wait_bounded(smem_u32(&never), 0, spin_limit);
         float* yf = yf0 + (S::YB == 2 ? b : 0) * S::YF_FLOATS;
-        const InstDesc* D = descs + find_inst(first, ninst, t);
-        const Geom g = D->g;
-        float* __restrict__ out = D->out;
+        const int inst = find_inst(first, ninst, t);
+        if (inst != cur) {
+            const InstDesc* D = descs + inst;
+            g = D->g;
+            out = D->out;
+            first_t = D->first_tile;
+            tiles_x = D->tiles_x;
+            cur = inst;
+        }
         const float* tile = buf + b * S::BUF_FLOATS;
-        const TileInfo ti = tile_info<TY>(t - D->first_tile, D->tiles_x);
+        const TileInfo ti = tile_info<TY>(t - first_t, tiles_x);
         const int ix = ti.x0 + lane, iy = ti.y0 + ty;
         const int s = lane + 4 + (ti.x0 - ti.bxa);  // smem column of the node
         const int r = ty + 3;                         // smem row of the node
@@ -287,13 +303,13 @@ __global__ void __launch_bounds__(32 * TY, 16 / TY) step_f32_kernel(const __grid
         for (int q = 1; q < NQ; ++q) {
             if (sgn_y(q) != 0) {
                 const float* col = yf + (yslot(q) * (TY + 1) + ty) * 32 + lane;
-                f[q] -= c.cy[q] * (col[32] - col[0]);
+                f[q] = fmaf(-c.cy[q], __fsub_rn(col[32], col[0]), f[q]);
             }
         }
         if (active) {
             float* o = out + (long long)(iy + GY) * g.px + (ix + GX);
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) o[q * g.plane] = f[q];
+            for (int q = 0; q < NQ; ++q) __stwb(o + q * g.plane, f[q]);  // global store
             if (has_images(g, ix, iy)) {
 #pragma unroll
                 for (int q = 0; q < NQ; ++q) write_images(out, g, q, ix, iy, f[q]);
