@@ -36,7 +36,14 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+NQ = 19  # velocities of the D2V19 set
 BYTES_PER_NODE = {"fp32": 152, "fp64": 304}  # 19 reads + 19 writes per node-update
+# FP32 lane operations of the FMA pipe per node-update (an fma counts as one):
+# 30 WENO5 faces x 34, moments and state 74, collision with the conservative
+# projection 223, flux differences 60 (the reciprocals run on the MUFU unit)
+FP32_OPS_PER_NODE = 1377
+# FP32 issue peak of the FMA pipes: 152 SMs x 128 lanes x 2070 MHz (max SM clock)
+FP32_LANE_PEAK_T = 152 * 128 * 2.070e9 / 1e12
 STEP_KERNEL_SOURCES = ["paper_1010_4124_gb300/csrc/klb_step_f32.cu", "paper_1010_4124_gb300/csrc/klb_device.cuh"]
 
 
@@ -55,15 +62,17 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def profiled_traffic(workload: str, precision: str):
-    """Bytes per launch from the committed ncu summary, if taken on the current kernel source."""
+def profiled_traffic(workload: str, precision: str, variant: int):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    if it was taken on the current kernel source and tile shape."""
     path = os.path.join(ROOT, "profiles", f"step_{precision}_{workload}.json")
     if not os.path.exists(path):
         return None
     d = json.load(open(path))
     if d.get("kernel_sha") != kernel_sha():
         return None
-    return d.get("traffic_bytes_per_launch")
+    t = d.get("traffic_bytes_per_launch")
+    return t.get(str(variant)) if isinstance(t, dict) else None
 
 
 class ClockSampler:
@@ -209,10 +218,24 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     cells = pb.nx * pb.ny
+    state_gb = NQ * pb.ny * pb.nx * (4 if prec == "fp32" else 8) / 1e9
     value = cells * args.steps * ws / (ms * 1e-3) / 1e9
     per_step_ms = ms / args.steps
     achieved = BYTES_PER_NODE[prec] * cells / (per_step_ms * 1e-3) / 1e9  # GB/s
     peak, peak_kind = measured_peaks()
+
+    kernel = "fdlb::step_f32_kernel" if prec == "fp32" else "fdlb::step_kernel<double>"
+    traffic = profiled_traffic(args.workload, prec, variant if prec == "fp32" else 0)
+    hbm_roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "peak_kind": peak_kind, "traffic": traffic,
+                "algorithmic_bytes_per_node": BYTES_PER_NODE[prec], "kernel": kernel}
+    alu_roof = None
+    if prec == "fp32":
+        ops = FP32_OPS_PER_NODE * cells / (per_step_ms * 1e-3) / 1e12
+        alu_roof = {"bound": "alu", "achieved": round(ops, 2), "peak": round(FP32_LANE_PEAK_T, 2),
+                    "unit": "T FP32 lane-ops/s (fma = 1)", "frac": round(ops / FP32_LANE_PEAK_T, 4),
+                    "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz",
+                    "traffic": traffic, "ops_per_node": FP32_OPS_PER_NODE, "kernel": kernel}
 
     # ---- end to end through the C ABI with host buffers (pinned)
     pin = [torch.from_numpy(a).pin_memory() for a in fields]
@@ -250,23 +273,26 @@ def run_ours(args):
                                f"periodic x / outflow y, dt=tau=1e-5, dx=dy=0.002",
                    "nx": pb.nx, "ny": pb.ny, "precision": prec, "diagnostics": "off in the timed steps",
                    "kernel_variant": variant if prec == "fp32" else 0,
-                   "l2": "inputs larger than L2 (2 x 1.29 GB of f per step)",
+                   "l2": f"inputs larger than L2 (2 x {state_gb:.2f} GB of f per step, L2 129 MB)",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
-        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
-                     "traffic": profiled_traffic(args.workload, prec),
-                     "algorithmic_bytes_per_node": BYTES_PER_NODE[prec],
-                     "kernel": "fdlb::step_f32_kernel" if prec == "fp32" else "fdlb::step_kernel<double>"},
+        "roofline": hbm_roof,
         "e2e": {"value": round(cells * args.steps * ws / e2e_s / 1e9, 4), "unit": "Gcell-updates/s",
                 "h2d_bytes_per_step": round(4 * 8 * cells / args.steps, 1),
                 "d2h_bytes_per_step": round(4 * 8 * cells / args.steps, 1)},
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    if alu_roof is not None:
+        # the FP32 step is bound by FP32 issue, not by HBM: the ALU roofline
+        # is the binding one, the HBM fraction is reported beside it
+        line["roofline"] = alu_roof
+        line["roofline_hbm"] = hbm_roof
     if rank == 0 and not args.no_sweep:
         line["sweep"] = sweep_measure(args.sweep_steps, torch)
+    if rank == 0 and not args.no_adjoint:
+        line["adjoint"] = [adjoint_measure(p, args.adjoint_steps, torch) for p in ("fp32", "fp64")]
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.workload, samples=3)
+        line["cpu_baseline"] = cpu_baseline(args.workload, samples=40, rows=1024)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -325,6 +351,52 @@ def sweep_measure(steps: int, torch):
             "looped_plain_gcell_s": round(cells * steps / t_loop / 1e9, 4),
             "speedup_vs_looped_plain": round(t_loop / t_batch, 3),
             "sizes": sorted({f"{pb.nx}x{pb.ny}" for pb in pbs})}
+
+
+def adjoint_measure(prec: str, steps: int, torch):
+    """The adjoint run of the 256 x 256 KHI (sampled every 10 steps,
+    objective KE + gamma): forward with a checkpoint every 45 steps plus the
+    reverse sweep, against the same with every state stored (checkpoint
+    every step: full-trajectory storage, no recomputation) and against two
+    plain forward runs of the step."""
+    from paper_1010_4124_gb300 import inputs, klb
+    pb = inputs.khi(256, 256, steps, sample_every=10)
+    dev = [torch.as_tensor(a, device="cuda").contiguous() for a in inputs.fields(pb)]
+    grads = tuple(torch.empty_like(dev[0]) for _ in range(4))
+
+    def run(ckpt):
+        with klb.KlbAdjoint.from_problem(pb, prec, checkpoint_every=ckpt) as adj:
+            adj.forward(*dev)
+            adj.backward(1.0, 1.0, out=grads)  # warm (allocations, graphs, caches)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            adj.forward(*dev)
+            adj.backward(1.0, 1.0, out=grads)
+            torch.cuda.synchronize()
+            return time.perf_counter() - t0
+
+    t_ckpt = run(45)
+    t_full = run(1)
+    stream = torch.cuda.Stream()
+    h = klb.Klb.from_problem(pb, precision=prec, stream=stream.cuda_stream)
+    h.init_fields(*dev)
+    h.step(20)
+    h.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    h.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    t_fwd = e0.elapsed_time(e1) * 1e-3
+    h.close()
+    state_mb = NQ * (pb.ny + 6) * ((pb.nx + 7 + 31) // 32 * 32) * (4 if prec == "fp32" else 8) / 1e6
+    return {"workload": f"KHI 256x256 {prec.upper()}, {steps} steps, sampled every 10, objective KE + gamma",
+            "precision": prec, "checkpoint_every": 45,
+            "adjoint_s": round(t_ckpt, 4), "full_storage_s": round(t_full, 4), "plain_forward_s": round(t_fwd, 4),
+            "adjoint_over_2x_forward": round(t_ckpt / (2 * t_fwd), 3),
+            "speedup_vs_full_storage": round(t_full / t_ckpt, 3),
+            "checkpoint_mb": round(((steps + 44) // 45) * state_mb, 1),
+            "full_storage_mb": round(steps * state_mb, 1)}
 
 
 def _band(pb, rows: int):
@@ -410,6 +482,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--sweep-steps", type=int, default=280)
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adjoint-steps", type=int, default=2000)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
