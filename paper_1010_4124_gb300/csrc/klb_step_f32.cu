@@ -4,19 +4,22 @@
 // whole grid.  Design, chosen so that every WENO5 face flux is evaluated
 // once, occupancy stays high and barriers are few:
 //
-//  * Persistent CTAs (one per SM, 16 warps) walk a list of tiles of 31
-//    columns x 16 rows.  Warp w owns tile row w; lane L owns column x0 + L.
-//  * Each tile (all 19 planes plus a 3-node halo, up to 4 columns on the left
-//    so the box starts on a 16-byte boundary) arrives by one 3-D TMA box load
+//  * Persistent CTAs (one per SM, 16 warps; or two of 8 warps) walk a list
+//    of tiles of 32 columns x 16 (or 8) rows.  Warp w owns tile row w; lane
+//    L owns array column 32 tx + L, so each warp-row store fills exactly one
+//    128-byte line and neighbouring tiles never write into the same line.
+//  * Each tile (all 19 planes plus a 3-node halo, 4 columns on the left so
+//    the box starts on a 16-byte boundary) arrives by one 3-D TMA box load
 //    (plain cp.async.bulk.tensor, no multicast) into one of two shared-memory
 //    buffers; the load of the next tile is issued before the current one is
 //    computed, so copies overlap computation.  Waits are bounded.
 //  * x fluxes: lane L evaluates the face on the LEFT of its column; its right
-//    face is lane L+1's left face, taken with one shuffle.  Lane 31 only
-//    supplies that face (31 output columns per warp).
+//    face is lane L+1's left face, taken with one shuffle.  The 18 faces on
+//    the right edge of the row are evaluated first, one per lane, and lane 31
+//    takes its right faces from them.
 //  * y fluxes: each thread evaluates the face BELOW its node and leaves it in
-//    shared memory; the faces above the tile's top row are evaluated by 12
-//    warps (one velocity each); after one barrier each node reads the face
+//    shared memory; the faces above the tile's top row are evaluated by six
+//    warps (two velocities each, packed); after one barrier each node reads the face
 //    above it from its upper neighbour.  That barrier is the only one per
 //    tile with 16-row tiles (two face buffers, used by alternate tiles); the
 //    8-row tiles (two CTAs per SM, one face buffer) add one at the tile's end.
@@ -31,8 +34,13 @@
 namespace fdlb {
 
 namespace v3 {
-constexpr int TW = 31;   // output columns per tile (one warp row)
-constexpr int SXB = 44;  // box width: 31 + 3 + 3 halo + up to 3 columns of 16-byte alignment, x4
+// A tile row is one warp: lane L holds array column 32 tx + L (interior column
+// 32 tx + L - GX), so every warp-row store covers one whole 128-byte line and
+// no two tiles share a line.  The tile's first lanes fall on the left ghost
+// columns for tx = 0 (inactive there).
+constexpr int TW = 32;   // columns per tile (one warp row)
+constexpr int SXB = 40;  // box width: array columns 32 tx - 4 .. 32 tx + 35 (halo of the 33 faces)
+constexpr int NXV = 18;  // velocities with an x component (all but the rest velocity)
 constexpr int NYV = 12;  // velocities with a y component
 static_assert((sizeof(float) * SXB) % 16 == 0, "box rows of 16-byte multiples");
 // tile of TW columns x TY rows (TY warps per CTA, 16 / TY CTAs per SM)
@@ -96,11 +104,27 @@ __device__ __forceinline__ float2 weno_pair(const float u[5], const float w[5], 
                            make_float2(u[3], w[3]), make_float2(u[4], w[4]), make_float2(eu, ew));
 }
 
+// The right-edge x-faces of a tile row (the left faces of array column
+// 32 tx + 32, next tile's lane 0): lane j < 18 evaluates velocity j + 1 and
+// leaves it in the warp's edge row; lane 31 takes its right faces from there.
+template <int TY>
+__device__ __forceinline__ void edge_faces(const StepConst<float>& c, const float* tile, int r, int lane,
+                                           float* edge) {
+    if (lane < v3::NXV) {
+        const int q = lane + 1;
+        const bool pos = sgn_x(q) > 0;
+        const int o = pos ? -3 : 2, d = pos ? 1 : -1;  // upwind stencil order (mirror for v_x < 0)
+        const float* a = tile + q * v3::Shape<TY>::PLANE + r * v3::SXB + (v3::TW + 4);
+        edge[lane] = ArithF32::weno(a[o], a[o + d], a[o + 2 * d], a[o + 3 * d], a[o + 4 * d], c.ex[q]);
+    }
+    __syncwarp();
+}
+
 // pass A for velocity Q with both components: its x-face and its y-face in
 // one packed evaluation; x flux into post[Q], bottom y-face into shared memory
 template <int TY, int Q>
 __device__ __forceinline__ void pass_a_xy(const StepConst<float>& c, const float* tile, float* yf, int r, int s,
-                                          int ty, int lane, float* post) {
+                                          int ty, int lane, const float* edge, float* post) {
     constexpr int SGX = sgn_x(Q), SGY = sgn_y(Q);
     static_assert(SGX != 0 && SGY != 0, "velocity with two components");
     const float* P = tile + Q * v3::Shape<TY>::PLANE;
@@ -108,20 +132,26 @@ __device__ __forceinline__ void pass_a_xy(const StepConst<float>& c, const float
     xst<SGX>(P, r, s, u);
     yst<SGY>(P, r, s, w);
     const float2 h = weno_pair(u, w, c.ex[Q], c.ey[Q]);
-    const float hr = __shfl_down_sync(0xffffffffu, h.x, 1);
+    float hr = __shfl_down_sync(0xffffffffu, h.x, 1);
+    if (lane == 31) hr = edge[Q - 1];  // the tile's right edge face
     post[Q] = fmaf(-c.cx[Q], __fsub_rn(hr, h.x), post[Q]);
     yf[(yslot(Q) * (TY + 1) + ty) * 32 + lane] = h.y;
 }
 // pass A for two velocities QA, QB with an x component only
 template <int TY, int QA, int QB>
-__device__ __forceinline__ void pass_a_xx(const StepConst<float>& c, const float* tile, int r, int s, float* post) {
+__device__ __forceinline__ void pass_a_xx(const StepConst<float>& c, const float* tile, int r, int s, int lane,
+                                          const float* edge, float* post) {
     static_assert(sgn_y(QA) == 0 && sgn_y(QB) == 0, "x-only velocities");
     float u[5], w[5];
     xst<sgn_x(QA)>(tile + QA * v3::Shape<TY>::PLANE, r, s, u);
     xst<sgn_x(QB)>(tile + QB * v3::Shape<TY>::PLANE, r, s, w);
     const float2 h = weno_pair(u, w, c.ex[QA], c.ex[QB]);
-    const float ra = __shfl_down_sync(0xffffffffu, h.x, 1);
-    const float rb = __shfl_down_sync(0xffffffffu, h.y, 1);
+    float ra = __shfl_down_sync(0xffffffffu, h.x, 1);
+    float rb = __shfl_down_sync(0xffffffffu, h.y, 1);
+    if (lane == 31) {  // the tile's right edge faces
+        ra = edge[QA - 1];
+        rb = edge[QB - 1];
+    }
     post[QA] = fmaf(-c.cx[QA], __fsub_rn(ra, h.x), post[QA]);
     post[QB] = fmaf(-c.cx[QB], __fsub_rn(rb, h.y), post[QB]);
 }
@@ -156,9 +186,10 @@ struct TileInfo {
 template <int TY>
 __device__ __forceinline__ TileInfo tile_info(int t, int tiles_x) {
     TileInfo ti;
-    ti.x0 = (t % tiles_x) * v3::TW;
+    const int tx = t % tiles_x;
+    ti.x0 = v3::TW * tx - GX;  // interior column of lane 0
     ti.y0 = (t / tiles_x) * TY;
-    ti.bxa = ti.x0 & ~3;  // array column of the box start (interior x0 - 4 is array x0): 16-byte aligned
+    ti.bxa = v3::TW * tx - 4;  // array column of the box start (16-byte aligned; -4 reads zeros)
     return ti;
 }
 
@@ -196,6 +227,7 @@ __global__ void __launch_bounds__(32 * TY, 16 / TY) step_f32_kernel(const __grid
     __shared__ __align__(8) uint64_t full[2];
     __shared__ __align__(8) uint64_t never;  // fault injection: a barrier nothing arrives on
     __shared__ int first[kMaxInstances];
+    __shared__ float edges[TY][v3::NXV];
 
     const int tid = threadIdx.x, ty = tid >> 5, lane = tid & 31;
     for (int i = tid; i < ninst; i += blockDim.x) first[i] = descs[i].first_tile;
@@ -252,9 +284,10 @@ __global__ void __launch_bounds__(32 * TY, 16 / TY) step_f32_kernel(const __grid
         const float* tile = buf + b * S::BUF_FLOATS;
         const TileInfo ti = tile_info<TY>(t - first_t, tiles_x);
         const int ix = ti.x0 + lane, iy = ti.y0 + ty;
-        const int s = lane + 4 + (ti.x0 - ti.bxa);  // smem column of the node
-        const int r = ty + 3;                         // smem row of the node
-        const bool active = lane < v3::TW && ix < g.nx && iy < g.ny;
+        const int s = lane + 4;  // smem column of the node
+        const int r = ty + 3;    // smem row of the node
+        const bool active = ix >= 0 && ix < g.nx && iy < g.ny;
+        float* const edge = edges[ty];
 
         float f[NQ];
 #pragma unroll
@@ -267,23 +300,24 @@ __global__ void __launch_bounds__(32 * TY, 16 / TY) step_f32_kernel(const __grid
             for (int j = 0; j < 8; ++j) dv[j] = (j == 4 || j == 5 || j == 7) ? fmax(dv[j], v[j]) : dv[j] + v[j];
         }
         ArithF32::collide(c, st, f);  // f <- post-collision values
+        edge_faces<TY>(c, tile, r, lane, edge);
         // x and y faces of the 12 velocities with two components, packed in pairs
-        pass_a_xy<TY, 1>(c, tile, yf, r, s, ty, lane, f);
-        pass_a_xy<TY, 2>(c, tile, yf, r, s, ty, lane, f);
-        pass_a_xy<TY, 4>(c, tile, yf, r, s, ty, lane, f);
-        pass_a_xy<TY, 5>(c, tile, yf, r, s, ty, lane, f);
-        pass_a_xy<TY, 7>(c, tile, yf, r, s, ty, lane, f);
-        pass_a_xy<TY, 8>(c, tile, yf, r, s, ty, lane, f);
-        pass_a_xy<TY, 10>(c, tile, yf, r, s, ty, lane, f);
-        pass_a_xy<TY, 11>(c, tile, yf, r, s, ty, lane, f);
-        pass_a_xy<TY, 13>(c, tile, yf, r, s, ty, lane, f);
-        pass_a_xy<TY, 14>(c, tile, yf, r, s, ty, lane, f);
-        pass_a_xy<TY, 16>(c, tile, yf, r, s, ty, lane, f);
-        pass_a_xy<TY, 17>(c, tile, yf, r, s, ty, lane, f);
+        pass_a_xy<TY, 1>(c, tile, yf, r, s, ty, lane, edge, f);
+        pass_a_xy<TY, 2>(c, tile, yf, r, s, ty, lane, edge, f);
+        pass_a_xy<TY, 4>(c, tile, yf, r, s, ty, lane, edge, f);
+        pass_a_xy<TY, 5>(c, tile, yf, r, s, ty, lane, edge, f);
+        pass_a_xy<TY, 7>(c, tile, yf, r, s, ty, lane, edge, f);
+        pass_a_xy<TY, 8>(c, tile, yf, r, s, ty, lane, edge, f);
+        pass_a_xy<TY, 10>(c, tile, yf, r, s, ty, lane, edge, f);
+        pass_a_xy<TY, 11>(c, tile, yf, r, s, ty, lane, edge, f);
+        pass_a_xy<TY, 13>(c, tile, yf, r, s, ty, lane, edge, f);
+        pass_a_xy<TY, 14>(c, tile, yf, r, s, ty, lane, edge, f);
+        pass_a_xy<TY, 16>(c, tile, yf, r, s, ty, lane, edge, f);
+        pass_a_xy<TY, 17>(c, tile, yf, r, s, ty, lane, edge, f);
         // x faces of the six velocities along the x axis, in pairs
-        pass_a_xx<TY, 3, 6>(c, tile, r, s, f);
-        pass_a_xx<TY, 9, 12>(c, tile, r, s, f);
-        pass_a_xx<TY, 15, 18>(c, tile, r, s, f);
+        pass_a_xx<TY, 3, 6>(c, tile, r, s, lane, edge, f);
+        pass_a_xx<TY, 9, 12>(c, tile, r, s, lane, edge, f);
+        pass_a_xx<TY, 15, 18>(c, tile, r, s, lane, edge, f);
         top_faces<TY, 0>(c, tile, yf, s, lane, ty);  // faces above the tile's top row
         // All faces are in shared memory and nobody reads this tile buffer
         // again (the next copy into it is issued after this barrier).
@@ -334,7 +368,7 @@ __global__ void __launch_bounds__(32 * TY) diag_f32_kernel(const StepConst<float
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const TileInfo ti = tile_info<TY>(t, tiles_x);
         const int ix = ti.x0 + lane, iy = ti.y0 + ty;
-        const bool active = lane < v3::TW && ix < g.nx && iy < g.ny;
+        const bool active = ix >= 0 && ix < g.nx && iy < g.ny;
         float fl[NQ];
 #pragma unroll
         for (int q = 0; q < NQ; ++q)
@@ -365,7 +399,7 @@ static int rows_of(int variant) { return variant == 1 ? 8 : 16; }
 
 void f32_tiles(int nx, int ny, int variant, int* tiles_x, int* ntiles) {
     const int ty = rows_of(variant);
-    *tiles_x = (nx + v3::TW - 1) / v3::TW;
+    *tiles_x = (nx + GX + v3::TW - 1) / v3::TW;  // array columns 0 .. nx + GX - 1
     *ntiles = *tiles_x * ((ny + ty - 1) / ty);
 }
 int f32_grid(int nx, int ny, int variant) {
