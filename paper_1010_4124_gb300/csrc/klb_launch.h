@@ -32,7 +32,7 @@ void f32_box(int variant, unsigned* bx, unsigned* by, unsigned* bz);
 // the buffer that receives the next one, its geometry and the index of its
 // first tile in the launch's tile index space.  Lives in device memory.
 constexpr int kMaxInstances = 256;
-struct alignas(64) InstDesc {
+struct InstDesc {  // aligned as its CUtensorMap member
     CUtensorMap map;
     float* out;
     Geom g;
