@@ -380,6 +380,9 @@ def adjoint_measure(prec: str, steps: int, torch):
     stream = torch.cuda.Stream()
     h = klb.Klb.from_problem(pb, precision=prec, stream=stream.cuda_stream)
     h.init_fields(*dev)
+    if prec == "fp32":
+        h.variant = pick_variant(h, stream, torch)
+        h.init_fields(*dev)
     h.step(20)
     h.sync()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -32,6 +32,7 @@ struct klb_adj {
     void* lam[2] = {nullptr, nullptr};
     void* Dx = nullptr;
     void* Dy = nullptr;
+    void* Nb = nullptr;            // per-node f^(0) sensitivity and u_y (5 * nx * ny)
     double* fields = nullptr;      // the initial fields (4 * nx * ny)
     double* dense = nullptr;       // staging for host / dense arrays (19 * nx * ny)
     std::vector<double> K;         // K_s of the forward run
@@ -83,15 +84,18 @@ static int vjp_step(klb_adj_t* a, const void* f, const void* lam_in, void* lam_o
     const StepConst<T>& c = *reinterpret_cast<const StepConst<T>*>(sizeof(T) == 8 ? (const void*)&h->cd
                                                                                    : (const void*)&h->cf);
     const Geom& g = h->g;
-    adj_faces_x_kernel<T><<<grid_of((long long)(g.nx + 1) * g.ny), 256, 0, h->stream>>>(
+    // one thread per (face, velocity) and per (node, velocity)
+    const long long n = (long long)g.nx * g.ny;
+    adj_faces_x_kernel<T><<<dim3(grid_of((long long)(g.nx + 1) * g.ny), NQ - 1), 256, 0, h->stream>>>(
         c, g, (const T*)f, (const T*)lam_in, (T*)a->Dx);
-    adj_faces_y_kernel<T><<<grid_of((long long)g.nx * (g.ny + 1)), 256, 0, h->stream>>>(
+    adj_faces_y_kernel<T><<<dim3(grid_of((long long)g.nx * (g.ny + 1)), 12), 256, 0, h->stream>>>(
         c, g, (const T*)f, (const T*)lam_in, (T*)a->Dy);
-    adj_gather_kernel<T><<<grid_of((long long)g.nx * g.ny), 256, 0, h->stream>>>(
-        c, g, (const T*)f, (const T*)lam_in, (const T*)a->Dx, (const T*)a->Dy, T(coef), (T*)lam_out);
+    adj_node_kernel<T><<<grid_of(n), 256, 0, h->stream>>>(c, g, (const T*)f, (const T*)lam_in, (T*)a->Nb);
+    adj_gather_kernel<T><<<dim3(grid_of(n), NQ), 256, 0, h->stream>>>(
+        c, g, (const T*)lam_in, (const T*)a->Nb, (const T*)a->Dx, (const T*)a->Dy, T(coef), (T*)lam_out);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return afail(a, KLB_E_CUDA, std::string("adjoint kernels: ") + cudaGetErrorString(e));
-    h->launches += 3;
+    h->launches += 4;
     return KLB_OK;
 }
 
@@ -213,6 +217,15 @@ int klb_adjoint_create(const klb_params* p, int64_t nsteps, int32_t checkpoint_e
         return afail(nullptr, r, std::string("forward grid: ") + klb_last_error(nullptr));
     }
     klb_t* h = a->h;
+    if (q.precision == KLB_FP32) {
+        // a grid with fewer 16-row tiles than two per SM steps faster with
+        // 8-row tiles (two CTAs per SM); both give the same bits
+        int dev = 0, sms = 1, tiles_x = 0, ntiles = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        f32_tiles(h->g.nx, h->g.ny, 0, &tiles_x, &ntiles);
+        if (ntiles < 2 * sms) klb_set_variant(h, 1);
+    }
     const size_t sb = state_bytes(h);
     const size_t nn = (size_t)h->g.nx * h->g.ny;
     bool ok = true;
@@ -223,6 +236,7 @@ int klb_adjoint_create(const klb_params* p, int64_t nsteps, int32_t checkpoint_e
     for (int k = 0; k < 2 && ok; ++k) ok = cudaMalloc(&a->lam[k], sb) == cudaSuccess;
     ok = ok && cudaMalloc(&a->Dx, h->esize * 5 * (size_t)18 * h->g.ny * (h->g.nx + 1)) == cudaSuccess;
     ok = ok && cudaMalloc(&a->Dy, h->esize * 5 * (size_t)12 * (h->g.ny + 1) * h->g.nx) == cudaSuccess;
+    ok = ok && cudaMalloc(&a->Nb, h->esize * 5 * nn) == cudaSuccess;
     ok = ok && cudaMalloc(&a->fields, sizeof(double) * 4 * nn) == cudaSuccess;
     ok = ok && cudaMalloc(&a->dense, sizeof(double) * NQ * nn) == cudaSuccess;
     if (!ok) {
@@ -246,6 +260,7 @@ void klb_adjoint_destroy(klb_adj_t* a) {
         if (a->lam[k]) cudaFree(a->lam[k]);
     if (a->Dx) cudaFree(a->Dx);
     if (a->Dy) cudaFree(a->Dy);
+    if (a->Nb) cudaFree(a->Nb);
     if (a->fields) cudaFree(a->fields);
     if (a->dense) cudaFree(a->dense);
     klb_destroy(a->h);

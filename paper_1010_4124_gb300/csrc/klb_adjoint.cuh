@@ -27,8 +27,9 @@ __device__ __forceinline__ void coeffs_and_slope(const StepConst<T>& c, T Tm, T 
     T s = 0, ds = 0;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        F[k + 1] = (T(24) * Tm * Tm * Tm - c.a4[k] * Tm * Tm + c.pk[k] * Tm) / c.den[k];
-        dF[k + 1] = (T(72) * Tm * Tm - T(2) * c.a4[k] * Tm + c.pk[k]) / c.den[k];
+        const T id = T(1) / c.den[k];
+        F[k + 1] = (T(24) * Tm * Tm * Tm - c.a4[k] * Tm * Tm + c.pk[k] * Tm) * id;
+        dF[k + 1] = (T(72) * Tm * Tm - T(2) * c.a4[k] * Tm + c.pk[k]) * id;
         s += F[k + 1];
         ds += dF[k + 1];
     }
@@ -43,9 +44,10 @@ __device__ __forceinline__ void coeffs_and_slope(const StepConst<T>& c, T Tm, T 
 //   beta_q = -2 alpha_q (h_q - h) / ((eps + sigma_q) S).
 template <typename T>
 __device__ __forceinline__ T weno5_grad(T a, T b, T c, T d, T e, T eps, T g[5]) {
-    const T h1 = (T(2) * a - T(7) * b + T(11) * c) / T(6);
-    const T h2 = (-b + T(5) * c + T(2) * d) / T(6);
-    const T h3 = (T(2) * c + T(5) * d - e) / T(6);
+    const T r6 = T(1) / T(6);
+    const T h1 = (T(2) * a - T(7) * b + T(11) * c) * r6;
+    const T h2 = (-b + T(5) * c + T(2) * d) * r6;
+    const T h3 = (T(2) * c + T(5) * d - e) * r6;
     const T t1 = a - T(2) * b + c, r1 = a - T(4) * b + T(3) * c;
     const T t2 = b - T(2) * c + d, r2 = b - d;
     const T t3 = c - T(2) * d + e, r3 = T(3) * c - T(4) * d + e;
@@ -53,13 +55,15 @@ __device__ __forceinline__ T weno5_grad(T a, T b, T c, T d, T e, T eps, T g[5]) 
     const T s1 = eps + k13 * t1 * t1 + T(0.25) * r1 * r1;
     const T s2 = eps + k13 * t2 * t2 + T(0.25) * r2 * r2;
     const T s3 = eps + k13 * t3 * t3 + T(0.25) * r3 * r3;
-    const T al1 = T(0.1) / (s1 * s1), al2 = T(0.6) / (s2 * s2), al3 = T(0.3) / (s3 * s3);
-    const T S = al1 + al2 + al3;
-    const T w1 = al1 / S, w2 = al2 / S, w3 = al3 / S;
+    // one reciprocal per indicator and one for the sum of the alphas
+    const T i1 = T(1) / s1, i2 = T(1) / s2, i3 = T(1) / s3;
+    const T al1 = T(0.1) * i1 * i1, al2 = T(0.6) * i2 * i2, al3 = T(0.3) * i3 * i3;
+    const T iS = T(1) / (al1 + al2 + al3);
+    const T w1 = al1 * iS, w2 = al2 * iS, w3 = al3 * iS;
     const T h = w1 * h1 + w2 * h2 + w3 * h3;
-    const T b1 = -T(2) * al1 * (h1 - h) / (s1 * S);
-    const T b2 = -T(2) * al2 * (h2 - h) / (s2 * S);
-    const T b3 = -T(2) * al3 * (h3 - h) / (s3 * S);
+    const T b1 = -T(2) * w1 * (h1 - h) * i1;
+    const T b2 = -T(2) * w2 * (h2 - h) * i2;
+    const T b3 = -T(2) * w3 * (h3 - h) * i3;
     // dsigma_q/dx: d(13/12 t^2 + r^2/4) = 13/6 t dt + r/2 dr
     const T k136 = T(13) / T(6);
     const T u1 = k136 * t1, v1 = T(0.5) * r1;  // coefficients of dt1, dr1
@@ -91,11 +95,12 @@ __device__ __forceinline__ Mom<T> moments_of(const StepConst<T>& c, const T* f) 
         e += f[q] * c.v2[q];
     }
     Mom<T> m;
+    const T ir = T(1) / r;
     m.rho = r;
-    m.ux = jx / r;
-    m.uy = jy / r;
+    m.ux = jx * ir;
+    m.uy = jy * ir;
     m.E = T(0.5) * e;
-    m.Tm = m.E / r - T(0.5) * (m.ux * m.ux + m.uy * m.uy);
+    m.Tm = m.E * ir - T(0.5) * (m.ux * m.ux + m.uy * m.uy);
     return m;
 }
 
@@ -107,20 +112,21 @@ __device__ __forceinline__ void feq_vjp_fields(const StepConst<T>& c, T rho, T u
     T F[4], dF[4];
     coeffs_and_slope(c, Tm, F, dF);
     const T u2 = ux * ux + uy * uy;
-    const T A = T(1) - u2 / (T(2) * Tm);
+    const T iT = T(1) / Tm;  // the only division
+    const T A = T(1) - T(0.5) * u2 * iT;
     T gr = 0, gx = 0, gy = 0, gT = 0;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
         const int k = ring_of(q);
-        const T w = (c.vx[q] * ux + c.vy[q] * uy) / Tm;
-        const T B = A * (T(1) + w) + T(0.5) * w * w + w * w * w / T(6);
+        const T w = (c.vx[q] * ux + c.vy[q] * uy) * iT;
+        const T B = A * (T(1) + w) + T(0.5) * w * w + w * w * w * (T(1) / T(6));
         const T dBw = A + w + T(0.5) * w * w;
         const T dBA = T(1) + w;
         const T lr = lam[q] * rho * F[k];
         gr += lam[q] * F[k] * B;
-        gx += lr * (dBw * c.vx[q] / Tm - dBA * ux / Tm);
-        gy += lr * (dBw * c.vy[q] / Tm - dBA * uy / Tm);
-        gT += lam[q] * rho * dF[k] * B + lr * (-dBw * w / Tm + dBA * u2 / (T(2) * Tm * Tm));
+        gx += lr * (dBw * c.vx[q] - dBA * ux) * iT;
+        gy += lr * (dBw * c.vy[q] - dBA * uy) * iT;
+        gT += lam[q] * rho * dF[k] * B + lr * (-dBw * w + T(0.5) * dBA * u2 * iT) * iT;
     }
     G[0] = gr;
     G[1] = gx;
@@ -155,66 +161,96 @@ __device__ __forceinline__ T lam_at(const T* lam, const Geom& g, int q, int i, i
     return lam[q * g.plane + (long long)(j + GY) * g.px + (i + GX)];
 }
 
-// x faces: thread (i, j), i in [0, nx] the face between nodes i-1 and i of row
-// j; for every velocity with v_x != 0, the five entries mu * v * dh/dF.
+// the velocity of y slot k (the 12 velocities with v_y != 0: directions 1, 2,
+// 4 and 5 of each ring) and the y slot of velocity q
+__device__ __forceinline__ int yvel_of(int k) {
+    const int d = k % 4;
+    return 1 + 6 * (k / 4) + (d < 2 ? d : d + 1);
+}
+__device__ __forceinline__ int yslot_of(int q) {
+    const int d = dir_of(q);
+    return 4 * (ring_of(q) - 1) + (d < 3 ? d - 1 : d - 2);
+}
+
+// Face-gradient buffers, structure of arrays: entry k of the face at
+// position t of velocity slot s lives at D[(5 s + k) nf + t].
+// x faces: thread t = (i, j), i in [0, nx] the face between nodes i-1 and i
+// of row j, for velocity q = blockIdx.y + 1 (every moving velocity has
+// v_x != 0): the five entries mu * v * dh/dF.
 template <typename T>
 __global__ void adj_faces_x_kernel(const StepConst<T> c, const Geom g, const T* __restrict__ f,
                                    const T* __restrict__ lam, T* __restrict__ D) {
     const long long nf = (long long)(g.nx + 1) * g.ny;
+    const int qx = blockIdx.y, q = qx + 1;
+    const T v = c.vx[q];
+    T* __restrict__ out = D + (long long)(5 * qx) * nf;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nf; t += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(t % (g.nx + 1)), j = (int)(t / (g.nx + 1));
-        int qx = 0;
-#pragma unroll 1
-        for (int q = 1; q < NQ; ++q) {
-            const T v = c.vx[q];
-            const T* row = f + q * g.plane + (long long)(j + GY) * g.px + GX;
-            T a, b, cc, d, e;
-            if (v > 0) {
-                a = v * row[i - 3]; b = v * row[i - 2]; cc = v * row[i - 1]; d = v * row[i]; e = v * row[i + 1];
-            } else {
-                a = v * row[i + 2]; b = v * row[i + 1]; cc = v * row[i]; d = v * row[i - 1]; e = v * row[i - 2];
-            }
-            T gr[5];
-            weno5_grad(a, b, cc, d, e, c.eps, gr);
-            const T mu = c.dt / c.dx * (lam_at(lam, g, q, i, j) - lam_at(lam, g, q, i - 1, j)) * v;
-            T* out = D + ((long long)(qx * g.ny + j) * (g.nx + 1) + i) * 5;
-#pragma unroll
-            for (int k = 0; k < 5; ++k) out[k] = mu * gr[k];
-            ++qx;
+        const T* row = f + q * g.plane + (long long)(j + GY) * g.px + GX;
+        T a, b, cc, d, e;
+        if (v > 0) {
+            a = v * row[i - 3]; b = v * row[i - 2]; cc = v * row[i - 1]; d = v * row[i]; e = v * row[i + 1];
+        } else {
+            a = v * row[i + 2]; b = v * row[i + 1]; cc = v * row[i]; d = v * row[i - 1]; e = v * row[i - 2];
         }
+        T gr[5];
+        weno5_grad(a, b, cc, d, e, c.eps, gr);
+        const T mu = c.dt / c.dx * (lam_at(lam, g, q, i, j) - lam_at(lam, g, q, i - 1, j)) * v;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) out[k * nf + t] = mu * gr[k];
     }
 }
 
-// y faces: thread (i, j), j in [0, ny] the face between rows j-1 and j of column i
+// y faces: thread t = (i, j), j in [0, ny] the face between rows j-1 and j of
+// column i, for the velocity of y slot blockIdx.y
 template <typename T>
 __global__ void adj_faces_y_kernel(const StepConst<T> c, const Geom g, const T* __restrict__ f,
                                    const T* __restrict__ lam, T* __restrict__ D) {
     const long long nf = (long long)g.nx * (g.ny + 1);
+    const int qy = blockIdx.y, q = yvel_of(qy);
+    const T v = c.vy[q];
+    T* __restrict__ out = D + (long long)(5 * qy) * nf;
+    const long long P = g.px;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nf; t += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(t % g.nx), j = (int)(t / g.nx);
-        int qy = 0;
-#pragma unroll 1
-        for (int q = 1; q < NQ; ++q) {
-            const T v = c.vy[q];
-            if (v == T(0)) continue;
-            const T* col = f + q * g.plane + (long long)GY * g.px + (i + GX);
-            const long long P = g.px;
-            T a, b, cc, d, e;
-            if (v > 0) {
-                a = v * col[(j - 3) * P]; b = v * col[(j - 2) * P]; cc = v * col[(j - 1) * P];
-                d = v * col[j * P]; e = v * col[(j + 1) * P];
-            } else {
-                a = v * col[(j + 2) * P]; b = v * col[(j + 1) * P]; cc = v * col[j * P];
-                d = v * col[(j - 1) * P]; e = v * col[(j - 2) * P];
-            }
-            T gr[5];
-            weno5_grad(a, b, cc, d, e, c.eps, gr);
-            const T mu = c.dt / c.dy * (lam_at(lam, g, q, i, j) - lam_at(lam, g, q, i, j - 1)) * v;
-            T* out = D + ((long long)(qy * (g.ny + 1) + j) * g.nx + i) * 5;
-#pragma unroll
-            for (int k = 0; k < 5; ++k) out[k] = mu * gr[k];
-            ++qy;
+        const T* col = f + q * g.plane + (long long)GY * g.px + (i + GX);
+        T a, b, cc, d, e;
+        if (v > 0) {
+            a = v * col[(j - 3) * P]; b = v * col[(j - 2) * P]; cc = v * col[(j - 1) * P];
+            d = v * col[j * P]; e = v * col[(j + 1) * P];
+        } else {
+            a = v * col[(j + 2) * P]; b = v * col[(j + 1) * P]; cc = v * col[j * P];
+            d = v * col[(j - 1) * P]; e = v * col[(j - 2) * P];
         }
+        T gr[5];
+        weno5_grad(a, b, cc, d, e, c.eps, gr);
+        const T mu = c.dt / c.dy * (lam_at(lam, g, q, i, j) - lam_at(lam, g, q, i, j - 1)) * v;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) out[k * nf + t] = mu * gr[k];
+    }
+}
+
+// Per node: the sensitivity of f^(0) carried to the moments (four values,
+// feq_vjp_moments) and u_y (for the source term), into N[5][nx * ny].
+template <typename T>
+__global__ void adj_node_kernel(const StepConst<T> c, const Geom g, const T* __restrict__ f,
+                                const T* __restrict__ lam, T* __restrict__ N) {
+    const long long n = (long long)g.nx * g.ny;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(t % g.nx), j = (int)(t / g.nx);
+        const long long at = (long long)(j + GY) * g.px + (i + GX);
+        T fl[NQ], ll[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            fl[q] = f[q * g.plane + at];
+            ll[q] = lam[q * g.plane + at];
+        }
+        const Mom<T> m = moments_of(c, fl);
+        T gm[4];
+        feq_vjp_moments(c, m, ll, gm);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) N[k * n + t] = gm[k];
+        N[4 * n + t] = m.uy;
     }
 }
 
@@ -244,63 +280,56 @@ __device__ __forceinline__ int images(int i, int n, int per, int lo_out, int hi_
     return m;
 }
 
-// lambda^n at every interior node: the BGK adjoint, the gathered face entries
-// and, with coef != 0, the source coef * dK/df of K = sum rho u_y^2 / 2.
+// lambda^n at interior node t = (i, j) for velocity q = blockIdx.y: the BGK
+// adjoint, the gathered face entries and, with coef != 0, the source
+// coef * dK/df of K = sum rho u_y^2 / 2.
 template <typename T>
-__global__ void adj_gather_kernel(const StepConst<T> c, const Geom g, const T* __restrict__ f,
-                                  const T* __restrict__ lam, const T* __restrict__ Dx, const T* __restrict__ Dy,
+__global__ void adj_gather_kernel(const StepConst<T> c, const Geom g, const T* __restrict__ lam,
+                                  const T* __restrict__ N, const T* __restrict__ Dx, const T* __restrict__ Dy,
                                   T coef, T* __restrict__ lam_out) {
     const long long n = (long long)g.nx * g.ny;
+    const long long nfx = (long long)(g.nx + 1) * g.ny, nfy = (long long)g.nx * (g.ny + 1);
+    const int q = blockIdx.y;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(t % g.nx), j = (int)(t / g.nx);
-        const long long at = (long long)(j + GY) * g.px + (i + GX);
-        T fl[NQ], ll[NQ];
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            fl[q] = f[q * g.plane + at];
-            ll[q] = lam[q * g.plane + at];
+        const long long at = q * g.plane + (long long)(j + GY) * g.px + (i + GX);
+        const T gm0 = N[t], gm1 = N[n + t], gm2 = N[2 * n + t], gm3 = N[3 * n + t];
+        T acc = (T(1) - c.relax) * lam[at] +
+                c.relax * (gm0 + gm1 * c.vx[q] + gm2 * c.vy[q] + gm3 * T(0.5) * c.v2[q]);
+        if (coef != T(0)) {
+            const T uy = N[4 * n + t];
+            acc += coef * (uy * c.vy[q] - T(0.5) * uy * uy);
         }
-        const Mom<T> m = moments_of(c, fl);
-        T gm[4];
-        feq_vjp_moments(c, m, ll, gm);
-        int px_[8], py_[8];
-        const int nxp = images(i, g.nx, g.bcx_lo == 0, g.bcx_lo == 1, g.bcx_hi == 1, px_);
-        const int nyp = images(j, g.ny, g.bcy_lo == 0, g.bcy_lo == 1, g.bcy_hi == 1, py_);
-        int qx = 0, qy = 0;
-#pragma unroll 1
-        for (int q = 0; q < NQ; ++q) {
-            T acc = (T(1) - c.relax) * ll[q] +
-                    c.relax * (gm[0] + gm[1] * c.vx[q] + gm[2] * c.vy[q] + gm[3] * T(0.5) * c.v2[q]);
-            if (coef != T(0)) acc += coef * (m.uy * c.vy[q] - T(0.5) * m.uy * m.uy);
-            if (c.vx[q] != T(0)) {
-                const T* Dq = Dx + (long long)(qx * g.ny + j) * (g.nx + 1) * 5;
-                const bool pos = c.vx[q] > 0;
-                for (int a = 0; a < nxp; ++a) {
-                    const int p = px_[a];
-                    // faces i' whose stencil holds position p, and p's slot k in it
-                    const int lo = pos ? p - 1 : p - 2, hi = pos ? p + 3 : p + 2;
-                    for (int ip = (lo < 0 ? 0 : lo); ip <= (hi > g.nx ? g.nx : hi); ++ip) {
-                        const int k = pos ? p - ip + 3 : ip + 2 - p;
-                        acc += Dq[ip * 5 + k];
-                    }
+        if (q > 0) {
+            int pos_[8];
+            const int np = images(i, g.nx, g.bcx_lo == 0, g.bcx_lo == 1, g.bcx_hi == 1, pos_);
+            const T* Dq = Dx + (long long)(5 * (q - 1)) * nfx + (long long)j * (g.nx + 1);
+            const bool pos = c.vx[q] > 0;
+            for (int a = 0; a < np; ++a) {
+                const int p = pos_[a];
+                // faces i' whose stencil holds position p, and p's slot k in it
+                const int lo = pos ? p - 1 : p - 2, hi = pos ? p + 3 : p + 2;
+                for (int ip = (lo < 0 ? 0 : lo); ip <= (hi > g.nx ? g.nx : hi); ++ip) {
+                    const int k = pos ? p - ip + 3 : ip + 2 - p;
+                    acc += Dq[k * nfx + ip];
                 }
-                ++qx;
             }
-            if (c.vy[q] != T(0)) {
-                const T* Dq = Dy + (long long)qy * (g.ny + 1) * g.nx * 5;
-                const bool pos = c.vy[q] > 0;
-                for (int a = 0; a < nyp; ++a) {
-                    const int p = py_[a];
-                    const int lo = pos ? p - 1 : p - 2, hi = pos ? p + 3 : p + 2;
-                    for (int jp = (lo < 0 ? 0 : lo); jp <= (hi > g.ny ? g.ny : hi); ++jp) {
-                        const int k = pos ? p - jp + 3 : jp + 2 - p;
-                        acc += Dq[((long long)jp * g.nx + i) * 5 + k];
-                    }
-                }
-                ++qy;
-            }
-            lam_out[q * g.plane + at] = acc;
         }
+        if (c.vy[q] != T(0)) {
+            int pos_[8];
+            const int np = images(j, g.ny, g.bcy_lo == 0, g.bcy_lo == 1, g.bcy_hi == 1, pos_);
+            const T* Dq = Dy + (long long)(5 * yslot_of(q)) * nfy + i;
+            const bool pos = c.vy[q] > 0;
+            for (int a = 0; a < np; ++a) {
+                const int p = pos_[a];
+                const int lo = pos ? p - 1 : p - 2, hi = pos ? p + 3 : p + 2;
+                for (int jp = (lo < 0 ? 0 : lo); jp <= (hi > g.ny ? g.ny : hi); ++jp) {
+                    const int k = pos ? p - jp + 3 : jp + 2 - p;
+                    acc += Dq[k * nfy + (long long)jp * g.nx];
+                }
+            }
+        }
+        lam_out[at] = acc;
     }
 }
 
