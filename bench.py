@@ -289,6 +289,8 @@ def run_ours(args):
         line["roofline_hbm"] = hbm_roof
     if rank == 0 and not args.no_sweep:
         line["sweep"] = sweep_measure(args.sweep_steps, torch)
+    if rank == 0 and not args.no_schemes:
+        line["schemes"] = schemes_measure(args.workload, 100, torch)
     if rank == 0 and not args.no_adjoint:
         line["adjoint"] = [adjoint_measure(p, args.adjoint_steps, torch) for p in ("fp32", "fp64")]
     if rank == 0 and not args.no_cpu_baseline:
@@ -402,6 +404,67 @@ def adjoint_measure(prec: str, steps: int, torch):
             "full_storage_mb": round(steps * state_mb, 1)}
 
 
+SOD_P_STAR = 0.285975  # star pressure of the gamma = 2 Sod problem (exact Riemann solution)
+
+
+def schemes_measure(workload: str, steps: int, torch):
+    """The convection schemes of the paper's comparison (Sec. III.B, Fig. 2):
+    FP32 step throughput of each on the bench workload, and the Sod tube
+    (200 x 4, FP64, 5000 steps to t = 0.1) run with each: the shock width
+    (10 %-90 % of the pressure jump, in cells) and the total variation of the
+    density (0.875 for the exact, monotone profile)."""
+    import numpy as np
+    from paper_1010_4124_gb300 import inputs, klb
+    names = ("weno5", "upwind1", "upwind2", "tvd")
+    pb = workload_problem(workload, steps)
+    fields = [np.ascontiguousarray(a) for a in inputs.fields(pb)]
+    stream = torch.cuda.Stream()
+    rate = {}
+    for sch in names:
+        with klb.Klb.from_problem(pb, precision="fp32", stream=stream.cuda_stream, scheme=sch) as h:
+            h.init_fields(*fields)
+            h.variant = pick_variant(h, stream, torch, steps=10)
+            h.step(3)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h.step(steps)
+            e1.record(stream)
+            e1.synchronize()
+            rate[sch] = round(pb.nx * pb.ny * steps / (e0.elapsed_time(e1) * 1e-3) / 1e9, 4)
+    sod = inputs.sod(200, 4, 5000)
+    sf = inputs.fields(sod)
+    x = (np.arange(sod.nx) + 0.5) * sod.dx
+    lo, hi = 0.1 + 0.1 * (SOD_P_STAR - 0.1), 0.1 + 0.9 * (SOD_P_STAR - 0.1)
+    width, tv = {}, {}
+    for sch in names:
+        with klb.Klb.from_problem(sod, precision="fp64", scheme=sch) as h:
+            h.init_fields(*sf)
+            h.step(sod.steps)
+            out = tuple(np.empty((sod.ny, sod.nx)) for _ in range(4))
+            h.moments(out)
+        r, p = out[0][0], out[0][0] * out[3][0]
+        if not (np.isfinite(r).all() and np.isfinite(p).all()):
+            width[sch], tv[sch] = None, None  # the run diverged
+            continue
+        sel = (x > 0.6) & (x < 0.8)
+        xx, pp = x[sel], p[sel]
+
+        def crossing(level):
+            i = np.where((pp[:-1] >= level) & (pp[1:] < level))[0]
+            if len(i) == 0:
+                return None
+            i = i[-1]
+            return xx[i] + sod.dx * (pp[i] - level) / (pp[i] - pp[i + 1])
+
+        a, b = crossing(lo), crossing(hi)
+        width[sch] = round((a - b) / sod.dx, 3) if a is not None and b is not None else None
+        tv[sch] = round(float(np.abs(np.diff(r)).sum()), 4)
+    return {"fp32_workload": f"{pb.nx}x{pb.ny}", "fp32_steps": steps, "fp32_gcell_s": rate,
+            "sod_fp64": {"workload": "Sod 200x4, dt = tau = 2e-5, 5000 steps (t = 0.1)",
+                         "shock_width_cells": width, "tv_rho": tv, "tv_rho_exact": 0.875,
+                         "null": "the run diverged (non-finite state)"}}
+
+
 def _band(pb, rows: int):
     """A full-width band of `rows` rows centred on the shear layer of the workload."""
     from paper_1010_4124_gb300 import inputs
@@ -486,6 +549,7 @@ def main():
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--sweep-steps", type=int, default=280)
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-schemes", action="store_true")
     ap.add_argument("--adjoint-steps", type=int, default=2000)
     args = ap.parse_args()
     if args.warmup < 3:

@@ -53,6 +53,16 @@ extern "C" {
 typedef enum { KLB_BC_PERIODIC = 0, KLB_BC_OUTFLOW = 1, KLB_BC_FIXED_EQ = 2 } klb_bc;
 typedef enum { KLB_FP32 = 0, KLB_FP64 = 1 } klb_prec;
 
+/* Convection scheme of the face fluxes h (Eq. 47).  The paper's method is
+ * WENO5 (Sec. III.A, Eqs. 48-55); it compares it near the Sod shock with three
+ * lower-order schemes (Sec. III.B, Fig. 2), which it names without formulas:
+ * with c the upwind node's value F_I, b = F_{I-1}, d = F_{I+1} (mirrored for a
+ * negative velocity component):
+ *   KLB_UPWIND1  h = c                                  (first-order upwind)
+ *   KLB_UPWIND2  h = c + (c - b) / 2                    (second-order upwind)
+ *   KLB_TVD2     h = c + minmod(c - b, d - c) / 2       (second-order TVD) */
+typedef enum { KLB_WENO5 = 0, KLB_UPWIND1 = 1, KLB_UPWIND2 = 2, KLB_TVD2 = 3 } klb_scheme;
+
 /* Problem statement of one run (Sec. III.B, Sec. IV of the paper). */
 typedef struct {
     int32_t nx, ny;           /* interior nodes in x (fastest) and y; >= 1 each */
@@ -67,12 +77,13 @@ typedef struct {
     int32_t diag_capacity;    /* samples kept on the device (0 = 4096); older samples are dropped */
     double eps;               /* WENO epsilon of Eq. 52; 0 selects the paper's 1e-6 */
     void* stream;             /* cudaStream_t to enqueue on; NULL = a stream owned by the handle */
+    int32_t scheme;           /* klb_scheme: convection scheme of the x and y fluxes (default WENO5) */
 } klb_params;
 
 typedef struct klb klb_t;
 
 /* Fill `p` with the defaults: v = {1,2,3}, all sides periodic, FP32,
- * sample_every 0, eps 1e-6, NULL stream.  nx, ny, dx, dy, dt, tau stay 0 and
+ * sample_every 0, eps 1e-6, NULL stream, WENO5.  nx, ny, dx, dy, dt, tau stay 0 and
  * must be set by the caller. */
 void klb_params_default(klb_params* p);
 

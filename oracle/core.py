@@ -18,6 +18,8 @@ from . import build as _build
 HERE = os.path.dirname(os.path.abspath(__file__))
 NQ = 19
 BC = {"periodic": 0, "outflow": 1, "fixed_eq": 2}
+# convection schemes (Sec. III.B, Fig. 2): WENO5 and the three it is compared with
+SCHEMES = {"weno5": 0, "upwind1": 1, "upwind2": 2, "tvd": 3}
 
 
 class _Params(C.Structure):
@@ -27,6 +29,7 @@ class _Params(C.Structure):
         ("v", C.c_double * 3),
         ("bc_x_lo", C.c_int32), ("bc_x_hi", C.c_int32), ("bc_y_lo", C.c_int32), ("bc_y_hi", C.c_int32),
         ("eps", C.c_double),
+        ("scheme", C.c_int32),
     ]
 
 
@@ -43,6 +46,7 @@ class Params:
     bc_x: tuple = ("periodic", "periodic")
     bc_y: tuple = ("periodic", "periodic")
     eps: float = 1e-6
+    scheme: str = "weno5"
 
     def c(self) -> _Params:
         p = _Params()
@@ -52,6 +56,7 @@ class Params:
         p.bc_x_lo, p.bc_x_hi = BC[self.bc_x[0]], BC[self.bc_x[1]]
         p.bc_y_lo, p.bc_y_hi = BC[self.bc_y[0]], BC[self.bc_y[1]]
         p.eps = self.eps
+        p.scheme = SCHEMES[self.scheme]
         return p
 
 
@@ -71,13 +76,14 @@ def lib(complex_step: bool = False):
         L.oklb_feq.argtypes = [vp, vp, vp, vp, vp, vp]
         L.oklb_moments.argtypes = [vp, vp, vp, vp, vp, vp]
         L.oklb_weno5_face.argtypes = [vp, C.c_double, vp]
+        L.oklb_face_flux.argtypes = [C.c_int32, vp, C.c_double, vp]
         L.oklb_fixed_ghosts.argtypes = [P, vp, vp, vp, vp, vp]
         L.oklb_init_feq.argtypes = [P, vp, vp, vp, vp, vp]
         L.oklb_fields.argtypes = [P, vp, vp, vp, vp, vp]
         L.oklb_step.argtypes = [P, vp, vp, vp]
         L.oklb_diag.argtypes = [P, vp, vp]
         L.oklb_run.argtypes = [P, vp, vp, C.c_int64, C.c_int32, vp, C.c_int64, C.POINTER(C.c_int64)]
-        for fn in ("oklb_velocity_set", "oklb_Fk", "oklb_feq", "oklb_moments", "oklb_weno5_face",
+        for fn in ("oklb_velocity_set", "oklb_Fk", "oklb_feq", "oklb_moments", "oklb_weno5_face", "oklb_face_flux",
                    "oklb_fixed_ghosts", "oklb_init_feq", "oklb_fields", "oklb_step", "oklb_diag", "oklb_run"):
             getattr(L, fn).restype = None
         _libs[key] = L
@@ -130,6 +136,14 @@ def moments(f, v=(1.0, 2.0, 3.0), cs: bool = False):
     outs = [np.zeros(1, dtype=_dt(cs)) for _ in range(4)]
     lib(cs).oklb_moments(_ptr(ff), _ptr(vv), *[_ptr(o) for o in outs])
     return tuple(o[0] for o in outs)
+
+
+def face_flux(scheme: str, F5, eps: float = 1e-6, cs: bool = False):
+    """h_{I+1/2} of `scheme` from the five upwind-ordered stencil values."""
+    ff = _arr(F5, cs)
+    h = np.zeros(1, dtype=_dt(cs))
+    lib(cs).oklb_face_flux(SCHEMES[scheme], _ptr(ff), float(eps), _ptr(h))
+    return h[0]
 
 
 def weno5_face(F5, eps: float = 1e-6, cs: bool = False):

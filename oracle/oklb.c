@@ -51,6 +51,8 @@ typedef struct {
     double v[3];
     int32_t bc_x_lo, bc_x_hi, bc_y_lo, bc_y_hi;
     double eps; /* WENO epsilon; the paper's value is 1e-6 (Eq. 52) */
+    int32_t scheme; /* convection scheme: 0 WENO5 (Sec. III.A), 1 first-order upwind,
+                       2 second-order upwind, 3 second-order TVD (minmod); Sec. III.B, Fig. 2 */
 } oklb_params;
 
 /* ------------------------------------------------------------------------ */
@@ -201,6 +203,44 @@ void oklb_weno5_face(const real F[5], double eps, real* h)
 }
 
 /* ------------------------------------------------------------------------ */
+/* The lower-order convection schemes the paper compares with WENO5 near the  */
+/* Sod shock (Sec. III.B, Fig. 2).  The paper names them and gives no         */
+/* formulas; these are the textbook forms, on the same upwind-ordered stencil */
+/* as weno5 (c = F_I the upwind node, b = F_{I-1}, d = F_{I+1}):              */
+/*   first-order upwind   h = F_I                                             */
+/*   second-order upwind  h = F_I + (F_I - F_{I-1}) / 2                       */
+/*   second-order TVD     h = F_I + minmod(F_I - F_{I-1}, F_{I+1} - F_I) / 2  */
+/* The TVD form is the minmod-limited (NND-type) scheme of the paper's        */
+/* reference for it.  For a negative velocity the mirrored stencil gives the  */
+/* upwind node I+1 and the differences towards I+2 and I, as for weno5.       */
+/* ------------------------------------------------------------------------ */
+static real minmod(real x, real y)
+{
+    /* the argument of smaller magnitude when both have the same sign, else 0
+       (decided on the real parts: the complex-step build differentiates the
+       branch that is taken) */
+    if (RE(x) > 0.0 && RE(y) > 0.0) return RE(x) < RE(y) ? x : y;
+    if (RE(x) < 0.0 && RE(y) < 0.0) return RE(x) > RE(y) ? x : y;
+    return 0.0;
+}
+
+static real face_flux(int scheme, real a, real b, real c, real d, real e, double eps)
+{
+    switch (scheme) {
+    case 1: return c;
+    case 2: return c + 0.5 * (c - b);
+    case 3: return c + 0.5 * minmod(c - b, d - c);
+    default: return weno5(a, b, c, d, e, eps);
+    }
+}
+
+/* exported for unit tests: the face flux of `scheme` (same stencil order) */
+void oklb_face_flux(int32_t scheme, const real F[5], double eps, real* h)
+{
+    *h = face_flux(scheme, F[0], F[1], F[2], F[3], F[4], eps);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Ghost nodes.  Three ghost layers per side (Sec. III.B, Eq. (57)).          */
 /*  periodic  : wrap-around (Sec. III.B and Sec. IV.A, y direction).          */
 /*  outflow   : zeroth-order extrapolation, Eqs. (63)-(64): every ghost node */
@@ -318,9 +358,10 @@ void oklb_fields(const oklb_params* p, const real* f, real* rho, real* ux, real*
 /* One time step, Sec. III.A, Eq. (47):                                      */
 /*   f^{n+1} = f^n - dt sum_alpha (h_{I+1/2} - h_{I-1/2}) / dr_alpha          */
 /*                 - (dt/tau) (f^n - f^{n,(0)}),                              */
-/* forward Euler in time, the alpha sum over x and y, h from weno5 applied to */
-/* F = v_alpha f with the upwind side given by the sign of v_alpha.  A zero   */
-/* velocity component carries no flux and is skipped.                         */
+/* forward Euler in time, the alpha sum over x and y, h from weno5 (or the    */
+/* scheme chosen in p->scheme) applied to F = v_alpha f with the upwind side  */
+/* given by the sign of v_alpha.  A zero velocity component carries no flux   */
+/* and is skipped.                                                             */
 /* Steps in order: ghost fill; moments -> F_k(T) -> f^(0) per node; WENO face  */
 /* fluxes in x and y; the update.                                              */
 /* ------------------------------------------------------------------------ */
@@ -359,10 +400,10 @@ void oklb_step(const oklb_params* p, const real* f, const real* fixed, real* fou
             for (int i = 0; i <= nx; ++i) {
                 real h = 0.0;
                 if (c > 0.0) { /* face between I = i-1 and i; stencil I-2..I+2 */
-                    h = weno5(c * PAD(q, j, i - 3), c * PAD(q, j, i - 2), c * PAD(q, j, i - 1),
+                    h = face_flux(p->scheme, c * PAD(q, j, i - 3), c * PAD(q, j, i - 2), c * PAD(q, j, i - 1),
                               c * PAD(q, j, i), c * PAD(q, j, i + 1), p->eps);
                 } else if (c < 0.0) { /* mirror stencil I+3..I-1 */
-                    h = weno5(c * PAD(q, j, i + 2), c * PAD(q, j, i + 1), c * PAD(q, j, i),
+                    h = face_flux(p->scheme, c * PAD(q, j, i + 2), c * PAD(q, j, i + 1), c * PAD(q, j, i),
                               c * PAD(q, j, i - 1), c * PAD(q, j, i - 2), p->eps);
                 }
                 hx[(size_t)q * ny * (nx + 1) + (size_t)j * (nx + 1) + i] = h;
@@ -377,10 +418,10 @@ void oklb_step(const oklb_params* p, const real* f, const real* fixed, real* fou
             for (int i = 0; i < nx; ++i) {
                 real h = 0.0;
                 if (c > 0.0) {
-                    h = weno5(c * PAD(q, j - 3, i), c * PAD(q, j - 2, i), c * PAD(q, j - 1, i),
+                    h = face_flux(p->scheme, c * PAD(q, j - 3, i), c * PAD(q, j - 2, i), c * PAD(q, j - 1, i),
                               c * PAD(q, j, i), c * PAD(q, j + 1, i), p->eps);
                 } else if (c < 0.0) {
-                    h = weno5(c * PAD(q, j + 2, i), c * PAD(q, j + 1, i), c * PAD(q, j, i),
+                    h = face_flux(p->scheme, c * PAD(q, j + 2, i), c * PAD(q, j + 1, i), c * PAD(q, j, i),
                               c * PAD(q, j - 1, i), c * PAD(q, j - 2, i), p->eps);
                 }
                 hy[(size_t)q * (ny + 1) * nx + (size_t)j * nx + i] = h;

@@ -205,6 +205,7 @@ int klb_adjoint_create(const klb_params* p, int64_t nsteps, int32_t checkpoint_e
     for (int b : bcs)
         if (b == KLB_BC_FIXED_EQ)
             return afail(nullptr, KLB_E_INVAL, "the adjoint supports periodic and outflow sides only");
+    if (p->scheme != KLB_WENO5) return afail(nullptr, KLB_E_INVAL, "the adjoint differentiates the WENO5 step only");
     klb_params q = *p;
     q.diag_capacity = (int32_t)(nsteps / p->sample_every + 1);
     klb_adj_t* a = new klb_adj();

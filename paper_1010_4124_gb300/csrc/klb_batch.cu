@@ -174,8 +174,8 @@ int klb_batch_create(const klb_params* ps, int n, klb_batch_t** out) {
         const klb_params& p = ps[i];
         if (p.precision != KLB_FP32) return bfail(nullptr, KLB_E_INVAL, "batches step FP32 grids");
         if (p.dx != p0.dx || p.dy != p0.dy || p.dt != p0.dt || p.tau != p0.tau || p.v[0] != p0.v[0] ||
-            p.v[1] != p0.v[1] || p.v[2] != p0.v[2] || p.eps != p0.eps)
-            return bfail(nullptr, KLB_E_INVAL, "instances of a batch must share dx, dy, dt, tau, v and eps");
+            p.v[1] != p0.v[1] || p.v[2] != p0.v[2] || p.eps != p0.eps || p.scheme != p0.scheme)
+            return bfail(nullptr, KLB_E_INVAL, "instances of a batch must share dx, dy, dt, tau, v, eps and scheme");
     }
     klb_batch_t* b = new klb_batch();
     auto cleanup = [&](int code, const std::string& msg) {

@@ -35,6 +35,7 @@ static int cuda_fail(klb_t* h, cudaError_t e, const char* where) {
 // ---------------------------------------------------------------------------
 template <typename T>
 static void fill_const(const klb_params& p, StepConst<T>& c) {
+    c.scheme = p.scheme;
     const double h = 0.5 * std::sqrt(3.0);
     const double cs[6] = {0.5, -0.5, -1.0, -0.5, 0.5, 1.0};  // cos(60 i deg), i = 1..6
     const double sn[6] = {h, h, 0.0, -h, -h, 0.0};            // sin(60 i deg)
@@ -166,6 +167,7 @@ void klb_params_default(klb_params* p) {
     p->bc_x_lo = p->bc_x_hi = p->bc_y_lo = p->bc_y_hi = KLB_BC_PERIODIC;
     p->precision = KLB_FP32;
     p->eps = 1e-6;
+    p->scheme = KLB_WENO5;
 }
 
 int klb_create(const klb_params* pin, klb_t** out) {
@@ -189,6 +191,7 @@ int klb_create(const klb_params* pin, klb_t** out) {
     if (p.precision != KLB_FP32 && p.precision != KLB_FP64) return fail(nullptr, KLB_E_INVAL, "unknown precision");
     if (p.sample_every < 0 || p.diag_capacity < 0) return fail(nullptr, KLB_E_INVAL, "negative diagnostics setting");
     if (p.eps < 0) return fail(nullptr, KLB_E_INVAL, "eps must be >= 0");
+    if (p.scheme < KLB_WENO5 || p.scheme > KLB_TVD2) return fail(nullptr, KLB_E_INVAL, "unknown convection scheme");
 
     const double vmax = std::max(p.v[0], std::max(p.v[1], p.v[2]));
     const double cfl = vmax * p.dt / std::min(p.dx, p.dy);

@@ -48,8 +48,18 @@ struct StepConst {
     // FP64 path (the paper's formulas term by term)
     T a4[3], pk[3], den[3];  // 4 (a_{k+1} + a_{k+2}), a_{k+1} a_{k+2}, 3 a_k (a_k - a_{k+1})(a_k - a_{k+2})
     T dt, dx, dy, eps;
-    T relax;  // dt / tau
+    T relax;     // dt / tau
+    int scheme;  // convection scheme (klb_scheme): 0 WENO5, 1 first-order upwind, 2 second-order upwind, 3 TVD
 };
+
+// minmod limiter of the second-order TVD scheme: the argument of smaller
+// magnitude when both have the same sign, else zero
+template <typename T>
+__device__ __forceinline__ T minmod(T x, T y) {
+    if (x > T(0) && y > T(0)) return x < y ? x : y;
+    if (x < T(0) && y < T(0)) return x > y ? x : y;
+    return T(0);
+}
 
 struct Geom {
     int nx, ny;          // interior size

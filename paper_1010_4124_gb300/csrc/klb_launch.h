@@ -46,6 +46,10 @@ cudaError_t launch_step_f32(const StepConst<float>& c, const InstDesc* descs, in
                             cudaStream_t stream);
 // set the kernels' attributes and query the device once (before any capture)
 cudaError_t prepare_f32_kernels();
+// the step with a lower-order convection scheme (c.scheme 1..3), rows 8 or 16
+cudaError_t launch_step_f32_lo(const StepConst<float>& c, const InstDesc* descs, int ninst, int ntiles,
+                               double* diag_partials, int* err, long long spin_limit, int inject, int rows, int grid,
+                               cudaStream_t stream);
 cudaError_t launch_diag_f32(const StepConst<float>& c, const Geom& g, const float* f, double* partials, int variant,
                             cudaStream_t s);
 

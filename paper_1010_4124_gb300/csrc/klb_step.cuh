@@ -47,28 +47,38 @@ struct SmemLayout {
     static constexpr size_t BYTES = TILE_BYTES + sizeof(T) * (HX + HY);
 };
 
-// WENO5 x-face between smem columns sx-1 and sx of row sy, plane P, for the
-// velocity component v of sign SGN.  The FP32 path reconstructs the unscaled
-// plane (eps / v^2, factor v in the update); the FP64 path reconstructs
-// F = v f exactly as Eq. (48) states it.
-template <typename T, int SX, int SGN>
-__device__ __forceinline__ T face_x(const T* P, int sy, int sx, T v, T eps) {
-    const T* r = P + sy * SX;
-    const T s = std::is_same<T, float>::value ? T(1) : v;
-    if (SGN > 0)
-        return Arith<T>::weno(s * r[sx - 3], s * r[sx - 2], s * r[sx - 1], s * r[sx], s * r[sx + 1], eps);
-    return Arith<T>::weno(s * r[sx + 2], s * r[sx + 1], s * r[sx], s * r[sx - 1], s * r[sx - 2], eps);
+// The face flux of the scheme c.scheme from the five upwind-ordered stencil
+// values of F = v f (Eqs. 48-55 for WENO5; the lower-order schemes of Fig. 2:
+// first-order upwind c, second-order upwind c + (c - b)/2, TVD
+// c + minmod(c - b, d - c)/2), each operation as the oracle writes it.
+template <typename T>
+__device__ __forceinline__ T face_flux(int scheme, T a, T b, T c, T d, T e, T eps) {
+    switch (scheme) {
+    case 1: return c;
+    case 2: return c + T(0.5) * (c - b);
+    case 3: return c + T(0.5) * minmod(c - b, d - c);
+    default: return Arith<T>::weno(a, b, c, d, e, eps);
+    }
 }
-// WENO5 y-face between smem rows sy-1 and sy of column sx, plane P.
+// x-face between smem columns sx-1 and sx of row sy, plane P, for the
+// velocity component v of sign SGN: the flux of F = v f exactly as Eq. (48)
+// states it.
 template <typename T, int SX, int SGN>
-__device__ __forceinline__ T face_y(const T* P, int sy, int sx, T v, T eps) {
-    const T* c = P + sx;
-    const T s = std::is_same<T, float>::value ? T(1) : v;
+__device__ __forceinline__ T face_x(const T* P, int sy, int sx, T v, T eps, int scheme) {
+    const T* r = P + sy * SX;
     if (SGN > 0)
-        return Arith<T>::weno(s * c[(sy - 3) * SX], s * c[(sy - 2) * SX], s * c[(sy - 1) * SX], s * c[sy * SX],
-                              s * c[(sy + 1) * SX], eps);
-    return Arith<T>::weno(s * c[(sy + 2) * SX], s * c[(sy + 1) * SX], s * c[sy * SX], s * c[(sy - 1) * SX],
-                          s * c[(sy - 2) * SX], eps);
+        return face_flux(scheme, v * r[sx - 3], v * r[sx - 2], v * r[sx - 1], v * r[sx], v * r[sx + 1], eps);
+    return face_flux(scheme, v * r[sx + 2], v * r[sx + 1], v * r[sx], v * r[sx - 1], v * r[sx - 2], eps);
+}
+// y-face between smem rows sy-1 and sy of column sx, plane P.
+template <typename T, int SX, int SGN>
+__device__ __forceinline__ T face_y(const T* P, int sy, int sx, T v, T eps, int scheme) {
+    const T* c = P + sx;
+    if (SGN > 0)
+        return face_flux(scheme, v * c[(sy - 3) * SX], v * c[(sy - 2) * SX], v * c[(sy - 1) * SX], v * c[sy * SX],
+                         v * c[(sy + 1) * SX], eps);
+    return face_flux(scheme, v * c[(sy + 2) * SX], v * c[(sy + 1) * SX], v * c[sy * SX], v * c[(sy - 1) * SX],
+                     v * c[(sy - 2) * SX], eps);
 }
 
 // The shared-memory face buffers carry values between threads across
@@ -89,18 +99,18 @@ __device__ __forceinline__ void velocity_update(const StepConst<T>& c, const Geo
     const T epsx = F32 ? c.ex[Q] : c.eps, epsy = F32 ? c.ey[Q] : c.eps;
     T hl = 0, hb = 0;
     if (SGX != 0) {
-        hl = face_x<T, SX, SGX>(P, sy, sx, c.vx[Q], epsx);
+        hl = face_x<T, SX, SGX>(P, sy, sx, c.vx[Q], epsx, c.scheme);
         hx[ty * (TX + 1) + tx] = hl;
     }
     if (SGY != 0) {
-        hb = face_y<T, SX, SGY>(P, sy, sx, c.vy[Q], epsy);
+        hb = face_y<T, SX, SGY>(P, sy, sx, c.vy[Q], epsy, c.scheme);
         hy[ty * TX + tx] = hb;
     }
     // tile edge faces: warp 0 the top row of y faces, warp 1 the right column of x faces
-    if (SGY != 0 && tid < TX) hy[TY * TX + tid] = face_y<T, SX, SGY>(P, TY + 3, tid + 4, c.vy[Q], epsy);
+    if (SGY != 0 && tid < TX) hy[TY * TX + tid] = face_y<T, SX, SGY>(P, TY + 3, tid + 4, c.vy[Q], epsy, c.scheme);
     if (SGX != 0 && tid >= 32 && tid < 32 + TY) {
         int r = tid - 32;
-        hx[r * (TX + 1) + TX] = face_x<T, SX, SGX>(P, r + 3, TX + 4, c.vx[Q], epsx);
+        hx[r * (TX + 1) + TX] = face_x<T, SX, SGX>(P, r + 3, TX + 4, c.vx[Q], epsx, c.scheme);
     }
     __syncthreads();
     T fn;

@@ -1,386 +1,9 @@
-// klb_step_f32.cu -- the fused FDLB time step in FP32 (production path).
-//
-// One launch = one forward-Euler step (Eq. 47 of arXiv:1010.4124) over the
-// whole grid.  Design, chosen so that every WENO5 face flux is evaluated
-// once, occupancy stays high and barriers are few:
-//
-//  * Persistent CTAs (one per SM, 16 warps; or two of 8 warps) walk a list
-//    of tiles of 32 columns x 16 (or 8) rows.  Warp w owns tile row w; lane
-//    L owns array column 32 tx + L, so each warp-row store fills exactly one
-//    128-byte line and neighbouring tiles never write into the same line.
-//  * Each tile (all 19 planes plus a 3-node halo, 4 columns on the left so
-//    the box starts on a 16-byte boundary) arrives by one 3-D TMA box load
-//    (plain cp.async.bulk.tensor, no multicast) into one of two shared-memory
-//    buffers; the load of the next tile is issued before the current one is
-//    computed, so copies overlap computation.  Waits are bounded.
-//  * x fluxes: lane L evaluates the face on the LEFT of its column; its right
-//    face is lane L+1's left face, taken with one shuffle.  The 18 faces on
-//    the right edge of the row are evaluated first, one per lane, and lane 31
-//    takes its right faces from them.
-//  * y fluxes: each thread evaluates the face BELOW its node and leaves it in
-//    shared memory; the faces above the tile's top row are evaluated by six
-//    warps (two velocities each, packed); after one barrier each node reads the face
-//    above it from its upper neighbour.  That barrier is the only one per
-//    tile with 16-row tiles (two face buffers, used by alternate tiles); the
-//    8-row tiles (two CTAs per SM, one face buffer) add one at the tile's end.
-//  * Per node: moments, F_k, f^(0) and the conservative BGK relaxation
-//    (ArithF32::collide) in registers, the flux divergence, and a coalesced
-//    store; nodes next to a periodic or outflow side also write their ghost
-//    images.  Optionally the diagnostics of the input nodes are reduced (FP64)
-//    per CTA; the stand-alone kernel below reproduces the same order.
-#include "klb_device.cuh"
-#include "klb_launch.h"
+// klb_step_f32.cu -- host side of the FP32 step (tile shapes, grid sizing,
+// launch) and its WENO5 instances; the lower-order schemes are instanced in
+// klb_step_f32_lo.cu.  The kernel itself is in klb_step_f32.cuh.
+#include "klb_step_f32.cuh"
 
 namespace fdlb {
-
-namespace v3 {
-// A tile row is one warp: lane L holds array column 32 tx + L (interior column
-// 32 tx + L - GX), so every warp-row store covers one whole 128-byte line and
-// no two tiles share a line.  The tile's first lanes fall on the left ghost
-// columns for tx = 0 (inactive there).
-constexpr int TW = 32;   // columns per tile (one warp row)
-constexpr int SXB = 40;  // box width: array columns 32 tx - 4 .. 32 tx + 35 (halo of the 33 faces)
-constexpr int NXV = 18;  // velocities with an x component (all but the rest velocity)
-constexpr int NYV = 12;  // velocities with a y component
-static_assert((sizeof(float) * SXB) % 16 == 0, "box rows of 16-byte multiples");
-// tile of TW columns x TY rows (TY warps per CTA, 16 / TY CTAs per SM)
-template <int TY>
-struct Shape {
-    static constexpr int NT = 32 * TY;
-    static constexpr int SYB = TY + 6;  // box height
-    static constexpr int PLANE = SXB * SYB;
-    static constexpr int BOX_FLOATS = NQ * PLANE;
-    static constexpr int BUF_FLOATS = (BOX_FLOATS + 31) / 32 * 32;  // 128-byte multiple (TMA destination)
-    static constexpr int YF_FLOATS = NYV * (TY + 1) * 32;
-    // face buffers: two (alternating tiles) when one CTA holds the SM, so that
-    // no barrier is needed at the end of a tile; one when two CTAs share it
-    static constexpr int YB = TY == 16 ? 2 : 1;
-    static constexpr size_t SMEM_BYTES = sizeof(float) * (2 * BUF_FLOATS + YB * YF_FLOATS) + 128;
-    static_assert((sizeof(float) * BUF_FLOATS) % 128 == 0, "TMA destination must stay 128-byte aligned");
-};
-}  // namespace v3
-
-// index of velocity q among the 12 with a non-zero y component
-__host__ __device__ constexpr int yslot(int q) {
-    int n = 0;
-    for (int k = 1; k < q; ++k) n += sgn_y(k) != 0 ? 1 : 0;
-    return n;
-}
-// the velocity in y slot k
-__host__ __device__ constexpr int yvel(int k) {
-    int n = 0;
-    for (int q = 1; q < NQ; ++q)
-        if (sgn_y(q) != 0) {
-            if (n == k) return q;
-            ++n;
-        }
-    return -1;
-}
-
-// the five upwind-ordered stencil values of the x-face on the left of smem
-// column s in row r of plane P
-template <int SGN>
-__device__ __forceinline__ void xst(const float* P, int r, int s, float v[5]) {  // (independent of TY)
-    const float* a = P + r * v3::SXB + s;
-    if (SGN > 0) {
-        v[0] = a[-3]; v[1] = a[-2]; v[2] = a[-1]; v[3] = a[0]; v[4] = a[1];
-    } else {
-        v[0] = a[2]; v[1] = a[1]; v[2] = a[0]; v[3] = a[-1]; v[4] = a[-2];
-    }
-}
-// ... of the y-face below smem row r (between rows r-1 and r) of column s
-template <int SGN>
-__device__ __forceinline__ void yst(const float* P, int r, int s, float v[5]) {
-    const float* a = P + r * v3::SXB + s;
-    constexpr int S = v3::SXB;
-    if (SGN > 0) {
-        v[0] = a[-3 * S]; v[1] = a[-2 * S]; v[2] = a[-S]; v[3] = a[0]; v[4] = a[S];
-    } else {
-        v[0] = a[2 * S]; v[1] = a[S]; v[2] = a[0]; v[3] = a[-S]; v[4] = a[-2 * S];
-    }
-}
-__device__ __forceinline__ float2 weno_pair(const float u[5], const float w[5], float eu, float ew) {
-    return ArithF32::weno2(make_float2(u[0], w[0]), make_float2(u[1], w[1]), make_float2(u[2], w[2]),
-                           make_float2(u[3], w[3]), make_float2(u[4], w[4]), make_float2(eu, ew));
-}
-
-// The right-edge x-faces of a tile row (the left faces of array column
-// 32 tx + 32, next tile's lane 0): lane j < 18 evaluates velocity j + 1 and
-// leaves it in the warp's edge row; lane 31 takes its right faces from there.
-template <int TY>
-__device__ __forceinline__ void edge_faces(const StepConst<float>& c, const float* tile, int r, int lane,
-                                           float* edge) {
-    if (lane < v3::NXV) {
-        const int q = lane + 1;
-        const bool pos = sgn_x(q) > 0;
-        const int o = pos ? -3 : 2, d = pos ? 1 : -1;  // upwind stencil order (mirror for v_x < 0)
-        const float* a = tile + q * v3::Shape<TY>::PLANE + r * v3::SXB + (v3::TW + 4);
-        edge[lane] = ArithF32::weno(a[o], a[o + d], a[o + 2 * d], a[o + 3 * d], a[o + 4 * d], c.ex[q]);
-    }
-    __syncwarp();
-}
-
-// pass A for velocity Q with both components: its x-face and its y-face in
-// one packed evaluation; x flux into post[Q], bottom y-face into shared memory
-template <int TY, int Q>
-__device__ __forceinline__ void pass_a_xy(const StepConst<float>& c, const float* tile, float* yf, int r, int s,
-                                          int ty, int lane, const float* edge, float* post) {
-    constexpr int SGX = sgn_x(Q), SGY = sgn_y(Q);
-    static_assert(SGX != 0 && SGY != 0, "velocity with two components");
-    const float* P = tile + Q * v3::Shape<TY>::PLANE;
-    float u[5], w[5];
-    xst<SGX>(P, r, s, u);
-    yst<SGY>(P, r, s, w);
-    const float2 h = weno_pair(u, w, c.ex[Q], c.ey[Q]);
-    float hr = __shfl_down_sync(0xffffffffu, h.x, 1);
-    if (lane == 31) hr = edge[Q - 1];  // the tile's right edge face
-    post[Q] = fmaf(-c.cx[Q], __fsub_rn(hr, h.x), post[Q]);
-    yf[(yslot(Q) * (TY + 1) + ty) * 32 + lane] = h.y;
-}
-// pass A for two velocities QA, QB with an x component only
-template <int TY, int QA, int QB>
-__device__ __forceinline__ void pass_a_xx(const StepConst<float>& c, const float* tile, int r, int s, int lane,
-                                          const float* edge, float* post) {
-    static_assert(sgn_y(QA) == 0 && sgn_y(QB) == 0, "x-only velocities");
-    float u[5], w[5];
-    xst<sgn_x(QA)>(tile + QA * v3::Shape<TY>::PLANE, r, s, u);
-    xst<sgn_x(QB)>(tile + QB * v3::Shape<TY>::PLANE, r, s, w);
-    const float2 h = weno_pair(u, w, c.ex[QA], c.ex[QB]);
-    float ra = __shfl_down_sync(0xffffffffu, h.x, 1);
-    float rb = __shfl_down_sync(0xffffffffu, h.y, 1);
-    if (lane == 31) {  // the tile's right edge faces
-        ra = edge[QA - 1];
-        rb = edge[QB - 1];
-    }
-    post[QA] = fmaf(-c.cx[QA], __fsub_rn(ra, h.x), post[QA]);
-    post[QB] = fmaf(-c.cx[QB], __fsub_rn(rb, h.y), post[QB]);
-}
-
-// the faces above the tile's top row, velocities of y slots K and K + 1 (one
-// packed evaluation), for lane's column
-template <int TY, int K>
-__device__ __forceinline__ void top_face_pair(const StepConst<float>& c, const float* tile, float* yf, int s,
-                                              int lane) {
-    constexpr int QA = yvel(K), QB = yvel(K + 1);
-    float u[5], w[5];
-    yst<sgn_y(QA)>(tile + QA * v3::Shape<TY>::PLANE, TY + 3, s, u);
-    yst<sgn_y(QB)>(tile + QB * v3::Shape<TY>::PLANE, TY + 3, s, w);
-    const float2 h = weno_pair(u, w, c.ey[QA], c.ey[QB]);
-    yf[(K * (TY + 1) + TY) * 32 + lane] = h.x;
-    yf[((K + 1) * (TY + 1) + TY) * 32 + lane] = h.y;
-}
-// warp w < 6 evaluates the top faces of y slots 2w and 2w + 1
-template <int TY, int K>
-__device__ __forceinline__ void top_faces(const StepConst<float>& c, const float* tile, float* yf, int s, int lane,
-                                          int w) {
-    static_assert(v3::NYV % 2 == 0 && v3::NYV / 2 <= TY, "one slot pair per warp");
-    if constexpr (K < v3::NYV) {
-        if (w == K / 2) top_face_pair<TY, K>(c, tile, yf, s, lane);
-        top_faces<TY, K + 2>(c, tile, yf, s, lane, w);
-    }
-}
-
-struct TileInfo {
-    int x0, y0, bxa;
-};
-template <int TY>
-__device__ __forceinline__ TileInfo tile_info(int t, int tiles_x) {
-    TileInfo ti;
-    const int tx = t % tiles_x;
-    ti.x0 = v3::TW * tx - GX;  // interior column of lane 0
-    ti.y0 = (t / tiles_x) * TY;
-    ti.bxa = v3::TW * tx - 4;  // array column of the box start (16-byte aligned; -4 reads zeros)
-    return ti;
-}
-
-// Tiles of several instances (grids of one batch, or the single grid of a
-// handle) form one index space: instance i owns tiles [first_i, first_i + n_i).
-// The CTA keeps the first-tile table in shared memory and finds a tile's
-// instance by binary search.
-__device__ __forceinline__ int find_inst(const int* first, int ninst, int t) {
-    int lo = 0, hi = ninst - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (first[mid] <= t) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
-// acquire a tensor map that the host wrote to global memory before the launch
-__device__ __forceinline__ void tensormap_acquire(const void* map) {
-    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
-}
-
-template <int TY>
-__global__ void __launch_bounds__(32 * TY, 16 / TY) step_f32_kernel(const __grid_constant__ StepConst<float> c,
-                                                                    const InstDesc* __restrict__ descs, int ninst,
-                                                                    int ntiles, double* __restrict__ diag_partials,
-                                                                    int* __restrict__ err, long long spin_limit,
-                                                                    int inject) {
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    // the launch reserves 128 spare bytes so that the buffers start on a
-    // 128-byte boundary of the shared window whatever precedes them
-    float* buf = reinterpret_cast<float*>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
-    using S = v3::Shape<TY>;
-    float* const yf0 = buf + 2 * S::BUF_FLOATS;
-    __shared__ __align__(8) uint64_t full[2];
-    __shared__ __align__(8) uint64_t never;  // fault injection: a barrier nothing arrives on
-    __shared__ int first[kMaxInstances];
-    __shared__ float edges[TY][v3::NXV];
-
-    const int tid = threadIdx.x, ty = tid >> 5, lane = tid & 31;
-    for (int i = tid; i < ninst; i += blockDim.x) first[i] = descs[i].first_tile;
-    auto issue = [&](int t, int b) {
-        const InstDesc* D = descs + find_inst(first, ninst, t);
-        const TileInfo ti = tile_info<TY>(t - D->first_tile, D->tiles_x);
-        const uint32_t bar = smem_u32(&full[b]);
-        tensormap_acquire(&D->map);
-        mbar_arrive_expect_tx(bar, (uint32_t)(sizeof(float) * S::BOX_FLOATS));
-        tma_load_3d(smem_u32(buf + b * S::BUF_FLOATS), &D->map, ti.bxa, ti.y0, 0, bar);
-    };
-    __syncthreads();
-    if (tid == 0) {
-        mbar_init(smem_u32(&full[0]), 1);
-        mbar_init(smem_u32(&full[1]), 1);
-        mbar_init(smem_u32(&never), 1);
-        fence_barrier_init();
-        fence_proxy_async();
-        if ((int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
-    }
-    __syncthreads();
-
-    double dv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    const bool diag = diag_partials != nullptr;
-    // fields of the instance of the current tile, read from global memory
-    // only when the instance changes (tiles of one instance are contiguous)
-    int cur = -1, first_t = 0, tiles_x = 1;
-    Geom g{};
-    float* out = nullptr;
-    int k = 0;  // local tile counter: buffer k & 1, phase (k >> 1) & 1
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
-        const int b = k & 1;
-        // prefetch the next tile into the other buffer (last read before the
-        // middle barrier of the previous tile)
-        if (tid == 0 && t + (int)gridDim.x < ntiles) {
-            fence_proxy_async();
-            issue(t + gridDim.x, b ^ 1);
-        }
-        // A wait that gives up is reported at the barrier in the middle of
-        // the tile; until then the thread computes on whatever the buffer
-        // holds (shared-memory reads only) and stores nothing.
-        bool late = !mbar_wait_bounded(smem_u32(&full[b]), (k >> 1) & 1, spin_limit);
-        if (inject) late = late || !mbar_wait_bounded(smem_u32(&never), 0, spin_limit);
-        float* yf = yf0 + (S::YB == 2 ? b : 0) * S::YF_FLOATS;
-        const int inst = find_inst(first, ninst, t);
-        if (inst != cur) {
-            const InstDesc* D = descs + inst;
-            g = D->g;
-            out = D->out;
-            first_t = D->first_tile;
-            tiles_x = D->tiles_x;
-            cur = inst;
-        }
-        const float* tile = buf + b * S::BUF_FLOATS;
-        const TileInfo ti = tile_info<TY>(t - first_t, tiles_x);
-        const int ix = ti.x0 + lane, iy = ti.y0 + ty;
-        const int s = lane + 4;  // smem column of the node
-        const int r = ty + 3;    // smem row of the node
-        const bool active = ix >= 0 && ix < g.nx && iy < g.ny;
-        float* const edge = edges[ty];
-
-        float f[NQ];
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) f[q] = tile[q * S::PLANE + r * v3::SXB + s];
-        const NodeEq<float> st = ArithF32::node_state(c, f);
-        if (diag) {
-            double v[8];
-            node_diag(st, active, v);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) dv[j] = (j == 4 || j == 5 || j == 7) ? fmax(dv[j], v[j]) : dv[j] + v[j];
-        }
-        ArithF32::collide(c, st, f);  // f <- post-collision values
-        edge_faces<TY>(c, tile, r, lane, edge);
-        // x and y faces of the 12 velocities with two components, packed in pairs
-        pass_a_xy<TY, 1>(c, tile, yf, r, s, ty, lane, edge, f);
-        pass_a_xy<TY, 2>(c, tile, yf, r, s, ty, lane, edge, f);
-        pass_a_xy<TY, 4>(c, tile, yf, r, s, ty, lane, edge, f);
-        pass_a_xy<TY, 5>(c, tile, yf, r, s, ty, lane, edge, f);
-        pass_a_xy<TY, 7>(c, tile, yf, r, s, ty, lane, edge, f);
-        pass_a_xy<TY, 8>(c, tile, yf, r, s, ty, lane, edge, f);
-        pass_a_xy<TY, 10>(c, tile, yf, r, s, ty, lane, edge, f);
-        pass_a_xy<TY, 11>(c, tile, yf, r, s, ty, lane, edge, f);
-        pass_a_xy<TY, 13>(c, tile, yf, r, s, ty, lane, edge, f);
-        pass_a_xy<TY, 14>(c, tile, yf, r, s, ty, lane, edge, f);
-        pass_a_xy<TY, 16>(c, tile, yf, r, s, ty, lane, edge, f);
-        pass_a_xy<TY, 17>(c, tile, yf, r, s, ty, lane, edge, f);
-        // x faces of the six velocities along the x axis, in pairs
-        pass_a_xx<TY, 3, 6>(c, tile, r, s, lane, edge, f);
-        pass_a_xx<TY, 9, 12>(c, tile, r, s, lane, edge, f);
-        pass_a_xx<TY, 15, 18>(c, tile, r, s, lane, edge, f);
-        top_faces<TY, 0>(c, tile, yf, s, lane, ty);  // faces above the tile's top row
-        // All faces are in shared memory and nobody reads this tile buffer
-        // again (the next copy into it is issued after this barrier).
-        if (__syncthreads_or(late)) {
-            if (tid == 0) {
-                atomicOr(err, ERR_TIMEOUT);
-                // let both copies that may be in flight land before leaving
-                mbar_wait_bounded(smem_u32(&full[b]), (k >> 1) & 1, kDrainPolls);
-                if (t + (int)gridDim.x < ntiles)
-                    mbar_wait_bounded(smem_u32(&full[b ^ 1]), ((k + 1) >> 1) & 1, kDrainPolls);
-            }
-            __syncthreads();
-            return;
-        }
-        // y fluxes from the faces below and above each node
-#pragma unroll
-        for (int q = 1; q < NQ; ++q) {
-            if (sgn_y(q) != 0) {
-                const float* col = yf + (yslot(q) * (TY + 1) + ty) * 32 + lane;
-                f[q] = fmaf(-c.cy[q], __fsub_rn(col[32], col[0]), f[q]);
-            }
-        }
-        if (active) {
-            float* o = out + (long long)(iy + GY) * g.px + (ix + GX);
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) __stwb(o + q * g.plane, f[q]);  // global store
-            if (has_images(g, ix, iy)) {
-#pragma unroll
-                for (int q = 0; q < NQ; ++q) write_images(out, g, q, ix, iy, f[q]);
-            }
-        }
-        // With two face buffers, the next tile writes the other one, and the
-        // one read here is written again only after every thread has passed
-        // the next tile's middle barrier.  With one, wait for all readers.
-        if (S::YB == 1) __syncthreads();
-    }
-    if (diag) diag_block_reduce<S::NT>(dv, diag_partials + 8ll * blockIdx.x);
-}
-
-// Stand-alone diagnostics of a state with the same tiles, per-CTA tile order
-// and block reduction as the fused path, so that both give the same bits.
-template <int TY>
-__global__ void __launch_bounds__(32 * TY) diag_f32_kernel(const StepConst<float> c, const Geom g, int tiles_x,
-                                                           int ntiles, const float* __restrict__ f,
-                                                           double* __restrict__ partials) {
-    const int tid = threadIdx.x, ty = tid >> 5, lane = tid & 31;
-    double dv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const TileInfo ti = tile_info<TY>(t, tiles_x);
-        const int ix = ti.x0 + lane, iy = ti.y0 + ty;
-        const bool active = ix >= 0 && ix < g.nx && iy < g.ny;
-        float fl[NQ];
-#pragma unroll
-        for (int q = 0; q < NQ; ++q)
-            fl[q] = active ? f[q * g.plane + (long long)(iy + GY) * g.px + (ix + GX)] : 1.f;
-        const NodeEq<float> st = ArithF32::node_state(c, fl);
-        double v[8];
-        node_diag(st, active, v);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) dv[j] = (j == 4 || j == 5 || j == 7) ? fmax(dv[j], v[j]) : dv[j] + v[j];
-    }
-    diag_block_reduce<32 * TY>(dv, partials + 8ll * blockIdx.x);
-}
 
 static int num_sms() {
     static int n = 0;
@@ -414,34 +37,10 @@ void f32_box(int variant, unsigned* bx, unsigned* by, unsigned* bz) {
     *bz = NQ;
 }
 
-template <int TY>
-static cudaError_t set_attr() {
-    static bool done = false;
-    if (!done) {
-        cudaError_t e = cudaFuncSetAttribute(step_f32_kernel<TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)v3::Shape<TY>::SMEM_BYTES);
-        if (e != cudaSuccess) return e;
-        done = true;
-    }
-    return cudaSuccess;
-}
-
 cudaError_t prepare_f32_kernels() {
     num_sms();
-    cudaError_t e = set_attr<8>();
-    return e != cudaSuccess ? e : set_attr<16>();
-}
-
-template <int TY>
-static cudaError_t launch_f32(const StepConst<float>& c, const InstDesc* descs, int ninst, int ntiles,
-                              double* diag_partials, int* err, long long spin_limit, int inject, int grid,
-                              cudaStream_t stream) {
-    cudaError_t e = set_attr<TY>();
-    if (e != cudaSuccess) return e;
-    step_f32_kernel<TY><<<grid, 32 * TY, v3::Shape<TY>::SMEM_BYTES, stream>>>(c, descs, ninst, ntiles,
-                                                                            diag_partials, err, spin_limit,
-                                                                            inject);
-    return cudaGetLastError();
+    cudaError_t e = set_attr_f32<8, 0>();
+    return e != cudaSuccess ? e : set_attr_f32<16, 0>();
 }
 
 cudaError_t launch_step_f32(const StepConst<float>& c, const InstDesc* descs, int ninst, int ntiles,
@@ -451,9 +50,12 @@ cudaError_t launch_step_f32(const StepConst<float>& c, const InstDesc* descs, in
     const int per_sm = 16 / rows_of(variant);
     const int grid = ntiles < num_sms() * per_sm ? ntiles : num_sms() * per_sm;
     if (grid < 1) return cudaSuccess;
+    if (c.scheme != 0)
+        return launch_step_f32_lo(c, descs, ninst, ntiles, diag_partials, err, spin_limit, inject,
+                                  rows_of(variant), grid, stream);
     if (rows_of(variant) == 8)
-        return launch_f32<8>(c, descs, ninst, ntiles, diag_partials, err, spin_limit, inject, grid, stream);
-    return launch_f32<16>(c, descs, ninst, ntiles, diag_partials, err, spin_limit, inject, grid, stream);
+        return launch_f32_t<8, 0>(c, descs, ninst, ntiles, diag_partials, err, spin_limit, inject, grid, stream);
+    return launch_f32_t<16, 0>(c, descs, ninst, ntiles, diag_partials, err, spin_limit, inject, grid, stream);
 }
 
 cudaError_t launch_diag_f32(const StepConst<float>& c, const Geom& g, const float* f, double* partials, int variant,

@@ -21,6 +21,7 @@ KLB_OK = 0
 ERRORS = {-1: "KLB_E_INVAL", -2: "KLB_E_NOMEM", -3: "KLB_E_CUDA", -4: "KLB_E_NONFINITE",
           -5: "KLB_E_DEVICE_TIMEOUT", -6: "KLB_E_STATE", -7: "KLB_E_IO"}
 BC = {"periodic": 0, "outflow": 1, "fixed_eq": 2}
+SCHEMES = {"weno5": 0, "upwind1": 1, "upwind2": 2, "tvd": 3}
 PREC = {"fp32": 0, "fp64": 1}
 
 
@@ -39,6 +40,7 @@ class klb_params(C.Structure):
         ("precision", C.c_int32), ("sample_every", C.c_int32), ("diag_capacity", C.c_int32),
         ("eps", C.c_double),
         ("stream", C.c_void_p),
+        ("scheme", C.c_int32),
     ]
 
 
@@ -130,7 +132,7 @@ def _ptr(a):
 
 def make_params(nx, ny, dx, dy, dt, tau, v=(1.0, 2.0, 3.0), bc_x=("periodic", "periodic"),
                 bc_y=("periodic", "periodic"), precision="fp32", sample_every=0, diag_capacity=0,
-                eps=1e-6, stream=None) -> klb_params:
+                eps=1e-6, stream=None, scheme="weno5") -> klb_params:
     p = klb_params()
     lib().klb_params_default(C.byref(p))
     p.nx, p.ny, p.dx, p.dy, p.dt, p.tau = nx, ny, dx, dy, dt, tau
@@ -142,6 +144,7 @@ def make_params(nx, ny, dx, dy, dt, tau, v=(1.0, 2.0, 3.0), bc_x=("periodic", "p
     p.diag_capacity = diag_capacity
     p.eps = eps
     p.stream = stream
+    p.scheme = SCHEMES[scheme]
     return p
 
 

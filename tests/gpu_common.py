@@ -8,9 +8,9 @@ from oracle import core
 from paper_1010_4124_gb300 import inputs, klb
 
 
-def oracle_params(pb: inputs.Problem, eps: float = 1e-6) -> core.Params:
+def oracle_params(pb: inputs.Problem, eps: float = 1e-6, scheme: str = "weno5") -> core.Params:
     return core.Params(nx=pb.nx, ny=pb.ny, dx=pb.dx, dy=pb.dy, dt=pb.dt, tau=pb.tau, v=pb.v,
-                       bc_x=pb.bc_x, bc_y=pb.bc_y, eps=eps)
+                       bc_x=pb.bc_x, bc_y=pb.bc_y, eps=eps, scheme=scheme)
 
 
 def gpu_handle(pb: inputs.Problem, precision: str, **kw) -> klb.Klb:

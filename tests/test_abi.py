@@ -43,15 +43,16 @@ def test_params_struct_layout_matches_header(lib):
     import subprocess
     import tempfile
     from paper_1010_4124_gb300 import klb
-    src = '#include "klb.h"\n#include <stdio.h>\n#include <stddef.h>\nint main(void){printf("%zu %zu\\n", sizeof(klb_params), offsetof(klb_params, stream));return 0;}\n'
+    src = '#include "klb.h"\n#include <stdio.h>\n#include <stddef.h>\nint main(void){printf("%zu %zu %zu\\n", sizeof(klb_params), offsetof(klb_params, stream), offsetof(klb_params, scheme));return 0;}\n'
     with tempfile.TemporaryDirectory() as d:
         c = os.path.join(d, "p.c")
         open(c, "w").write(src)
         exe = os.path.join(d, "p")
         subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
-        size, off = map(int, subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split())
+        size, off, off_s = map(int, subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split())
     assert C.sizeof(klb.klb_params) == size
     assert klb.klb_params.stream.offset == off
+    assert klb.klb_params.scheme.offset == off_s
 
 
 def test_create_rejects_bad_params_without_gpu(lib):
@@ -67,4 +68,23 @@ def test_create_rejects_bad_params_without_gpu(lib):
     p = klb.make_params(8, 8, 0.01, 0.01, 1e-5, 1e-5, v=(1.0, 1.0, 3.0))
     with pytest.raises(klb.KlbError) as e:
         klb.Klb(p)
+    assert e.value.code == -1
+
+
+def test_scheme_validation_without_gpu(lib):
+    # an unknown convection scheme is refused before any device work; a batch
+    # must share one scheme; the adjoint differentiates the WENO5 step only
+    from paper_1010_4124_gb300 import klb
+    p = klb.make_params(8, 8, 0.01, 0.01, 1e-5, 1e-5)
+    p.scheme = 7
+    with pytest.raises(klb.KlbError) as e:
+        klb.Klb(p)
+    assert e.value.code == -1 and "scheme" in str(e.value)
+    ps = [klb.make_params(8, 8, 0.01, 0.01, 1e-5, 1e-5, scheme=s) for s in ("tvd", "upwind1")]
+    with pytest.raises(klb.KlbError) as e:
+        klb.KlbBatch(ps)
+    assert e.value.code == -1
+    q = klb.make_params(8, 8, 0.01, 0.01, 1e-5, 1e-5, scheme="upwind1", sample_every=1)
+    with pytest.raises(klb.KlbError) as e:
+        klb.KlbAdjoint(q, 4, 2)
     assert e.value.code == -1
