@@ -44,7 +44,8 @@ BYTES_PER_NODE = {"fp32": 152, "fp64": 304}  # 19 reads + 19 writes per node-upd
 FP32_OPS_PER_NODE = 1377
 # FP32 issue peak of the FMA pipes: 152 SMs x 128 lanes x 2070 MHz (max SM clock)
 FP32_LANE_PEAK_T = 152 * 128 * 2.070e9 / 1e12
-STEP_KERNEL_SOURCES = ["paper_1010_4124_gb300/csrc/klb_step_f32.cu", "paper_1010_4124_gb300/csrc/klb_device.cuh"]
+STEP_KERNEL_SOURCES = ["paper_1010_4124_gb300/csrc/klb_step_f32.cuh", "paper_1010_4124_gb300/csrc/klb_step_f32.cu",
+                       "paper_1010_4124_gb300/csrc/klb_device.cuh"]
 
 
 def kernel_sha() -> str:

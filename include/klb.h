@@ -130,6 +130,15 @@ int klb_sync(klb_t* h);
  * skip that field.  Synchronises. */
 int klb_moments(klb_t* h, double* rho, double* ux, double* uy, double* T, int on_device);
 
+/* Averaged density profile of the mixing layer (Sec. IV.A, Fig. 4): the
+ * density averaged along the interface, which in this library lies along x
+ * (the periodic axis of the Kelvin-Helmholtz set-up):
+ *   out[j] = (1/nx) sum_i rho(x_i, y_j),  j = 0 .. ny-1,  rho = sum_q f_q,
+ * summed in FP64 in a fixed order.  out is caller-owned, ny doubles, on the
+ * host (on_device = 0) or the device (on_device = 1).  Synchronises.  Errors:
+ * KLB_E_INVAL, KLB_E_STATE (before klb_init_fields), KLB_E_CUDA. */
+int klb_mean_density(klb_t* h, double* out, int on_device);
+
 /* Diagnostics series (Sec. IV): one record of 7 doubles per sample, taken on
  * the states after 0, s, 2s, ... steps (s = sample_every):
  *   [0] sum rho, [1] sum rho u_x, [2] sum rho u_y, [3] sum rho (T + |u|^2/2),

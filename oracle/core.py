@@ -82,9 +82,11 @@ def lib(complex_step: bool = False):
         L.oklb_fields.argtypes = [P, vp, vp, vp, vp, vp]
         L.oklb_step.argtypes = [P, vp, vp, vp]
         L.oklb_diag.argtypes = [P, vp, vp]
+        L.oklb_mean_density.argtypes = [P, vp, vp]
         L.oklb_run.argtypes = [P, vp, vp, C.c_int64, C.c_int32, vp, C.c_int64, C.POINTER(C.c_int64)]
         for fn in ("oklb_velocity_set", "oklb_Fk", "oklb_feq", "oklb_moments", "oklb_weno5_face", "oklb_face_flux",
-                   "oklb_fixed_ghosts", "oklb_init_feq", "oklb_fields", "oklb_step", "oklb_diag", "oklb_run"):
+                   "oklb_fixed_ghosts", "oklb_init_feq", "oklb_fields", "oklb_step", "oklb_diag", "oklb_run",
+                   "oklb_mean_density"):
             getattr(L, fn).restype = None
         _libs[key] = L
     return _libs[key]
@@ -199,6 +201,15 @@ def diag(p: Params, f, cs: bool = False):
     pc = p.c()
     lib(cs).oklb_diag(C.byref(pc), _ptr(ff), _ptr(d))
     return d
+
+
+def mean_density(p: Params, f, cs: bool = False):
+    """The averaged density profile rho_bar[ny] (see oklb_mean_density)."""
+    ff = _arr(f, cs)
+    out = np.zeros(p.ny, dtype=_dt(cs))
+    pc = p.c()
+    lib(cs).oklb_mean_density(C.byref(pc), _ptr(ff), _ptr(out))
+    return out
 
 
 def run(p: Params, f, nsteps: int, fixed=None, sample_every: int = 0, cs: bool = False):

@@ -450,6 +450,28 @@ void oklb_step(const oklb_params* p, const real* f, const real* fixed, real* fou
 }
 
 /* ------------------------------------------------------------------------ */
+/* Averaged density profile of the mixing layer (Sec. IV.A, the profile of   */
+/* Fig. 4): the density averaged along the direction of the interface.  In   */
+/* this code the interface lies along x (the periodic axis), so              */
+/*   rho_bar(y_j) = (1/nx) sum_i rho(x_i, y_j),  rho = sum_q f_q (Eq. 10),   */
+/* the integral over one period by the rectangle rule.                       */
+/* ------------------------------------------------------------------------ */
+void oklb_mean_density(const oklb_params* p, const real* f, real* out)
+{
+    const int nx = p->nx, ny = p->ny;
+    const size_t n = (size_t)nx * ny;
+    for (int j = 0; j < ny; ++j) {
+        real s = 0.0;
+        for (int i = 0; i < nx; ++i) {
+            real rho = 0.0;
+            for (int q = 0; q < NQ; ++q) rho += f[(size_t)q * n + (size_t)j * nx + i];
+            s += rho;
+        }
+        out[j] = s / nx;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Diagnostics of one state (Sec. IV: E_x = rho u^2 / 2 of the cross-stream   */
 /* component and its maximum over the domain; conservation sums):            */
 /*  d[0] = sum rho, d[1] = sum rho u_x, d[2] = sum rho u_y,                   */

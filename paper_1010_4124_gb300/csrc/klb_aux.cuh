@@ -128,6 +128,39 @@ __global__ void __launch_bounds__(TX* TY) diag_partials_kernel(const StepConst<T
     diag_block_reduce<TX * TY>(v, partials + 8ll * (blockIdx.y * gridDim.x + blockIdx.x));
 }
 
+// Averaged density profile (Sec. IV.A): rho_bar[j] = (1/nx) sum_i rho(i, j),
+// the interface lying along x.  One CTA per row; rho = sum_q f_q and the row
+// sum in FP64, reduced in a fixed order (deterministic).
+template <typename T>
+__global__ void __launch_bounds__(256) mean_density_kernel(const Geom g, const T* __restrict__ f,
+                                                           double* __restrict__ out) {
+    __shared__ double part[8];
+    const int j = blockIdx.x;
+    const T* row = f + (long long)(j + GY) * g.px + GX;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
+        double r = 0.0;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) r += (double)row[q * g.plane + i];
+        s += r;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+        out[j] = t / g.nx;
+    }
+}
+
+template <typename T>
+cudaError_t launch_mean_density(const Geom& g, const T* f, double* out, cudaStream_t s) {
+    mean_density_kernel<T><<<g.ny, 256, 0, s>>>(g, f, out);
+    return cudaGetLastError();
+}
+
 static inline int grid_for(long long n, int threads) {
     long long b = (n + threads - 1) / threads;
     if (b < 1) b = 1;
@@ -172,6 +205,7 @@ cudaError_t launch_diag_partials_tiles(const StepConst<T>& c, const Geom& g, con
 }
 
 #define KLB_AUX_INST(T)                                                                                  \
+    template cudaError_t launch_mean_density<T>(const Geom&, const T*, double*, cudaStream_t);                  \
     template cudaError_t launch_init_feq<T>(const StepConst<T>&, const Geom&, const double*, const double*,     \
                                             const double*, const double*, T*, T*, cudaStream_t);              \
     template cudaError_t launch_fixed_ghosts<T>(const StepConst<T>&, const Geom&, const double*, const double*, \

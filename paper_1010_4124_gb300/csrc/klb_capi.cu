@@ -532,6 +532,20 @@ int klb_moments(klb_t* h, double* rho, double* ux, double* uy, double* T, int on
     return klb_sync(h);
 }
 
+int klb_mean_density(klb_t* h, double* out, int on_device) {
+    if (!h) return KLB_E_INVAL;
+    if (!out) return fail(h, KLB_E_INVAL, "NULL argument");
+    if (!h->initialized) return fail(h, KLB_E_STATE, "klb_mean_density before klb_init_fields");
+    double* d = on_device ? out : h->fields_dev;  // staging: fields_dev holds 4 nx ny >= ny doubles
+    cudaError_t e = h->p.precision == KLB_FP64
+                        ? launch_mean_density<double>(h->g, (const double*)h->buf[h->cur], d, h->stream)
+                        : launch_mean_density<float>(h->g, (const float*)h->buf[h->cur], d, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "mean density kernel");
+    h->launches += 1;
+    if (!on_device) CK(h, cudaMemcpyAsync(out, d, h->g.ny * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    return klb_sync(h);
+}
+
 int klb_diagnostics(klb_t* h, double* out, int64_t cap, int64_t* count) {
     if (!h || !count || (cap > 0 && !out)) return h ? fail(h, KLB_E_INVAL, "NULL argument") : KLB_E_INVAL;
     if (!h->initialized) return fail(h, KLB_E_STATE, "klb_diagnostics before klb_init_fields");

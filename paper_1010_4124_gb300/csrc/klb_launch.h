@@ -67,6 +67,9 @@ cudaError_t launch_set_f(const Geom& g, const double* src, T* dst, cudaStream_t 
 template <typename T>
 cudaError_t launch_get_f(const Geom& g, const T* src, double* dst, cudaStream_t s);
 // macroscopic fields of the interior
+// rho_bar[j] = (1/nx) sum_i rho(i, j) for j < ny (klb_aux.cuh)
+template <typename T>
+cudaError_t launch_mean_density(const Geom& g, const T* f, double* out, cudaStream_t s);
 template <typename T>
 cudaError_t launch_fields(const StepConst<T>& c, const Geom& g, const T* f, double* rho, double* ux, double* uy,
                           double* Tm, cudaStream_t s);

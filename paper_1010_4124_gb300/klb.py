@@ -100,6 +100,7 @@ def lib():
             "klb_adjoint_grid": (vp, [vp]),
             "klb_adjoint_last_error": (C.c_char_p, [vp]),
             "klb_diagnostics_static": (C.c_int, [vp, i32, i32, i32, i64, i64, vp, vp, vp]),
+            "klb_mean_density": (C.c_int, [vp, vp, i32]),
             "klb_diagnostics_static_error": (C.c_char_p, []),
         }
         for name, (res, args) in sig.items():
@@ -220,6 +221,14 @@ class Klb:
         ptrs = [_ptr(a) for a in out]
         ond = {p[1] for p in ptrs if p[0] is not None}
         _check(self.h, lib().klb_moments(self.h, *[p[0] for p in ptrs], ond.pop() if ond else 0))
+        return out
+
+    def mean_density(self, out=None):
+        """The averaged density profile rho_bar[ny] (mean of rho along x)."""
+        if out is None:
+            out = np.empty(self.ny)
+        pa, dev = _ptr(out)
+        _check(self.h, lib().klb_mean_density(self.h, pa, dev))
         return out
 
     def diagnostics(self, cap: int = 1 << 16):

@@ -321,3 +321,25 @@ def test_fp32_variants_are_bitwise_identical():
             h.step(30)
             out.append(h.get_f())
     assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_mean_density_profile(prec, tol):
+    # the averaged density profile (Sec. IV.A) of the state the CUDA path
+    # reaches: equal to the oracle's profile of that same state (summation
+    # order only), and to the profile of the oracle's own run
+    pb = inputs.khi(96, 64, 50, Dv=3.0, Drho=5.0)
+    p = oracle_params(pb)
+    fields = inputs.fields(pb)
+    ref, _ = core.run(p, core.init_feq(p, *fields), 50)
+    with gpu_handle(pb, prec) as h:
+        h.init_fields(*fields)
+        h.step(50)
+        md = h.mean_density()
+        got = h.get_f()
+        import torch
+        dev = torch.empty(pb.ny, dtype=torch.float64, device="cuda")
+        h.mean_density(dev)
+        np.testing.assert_array_equal(dev.cpu().numpy(), md)
+    np.testing.assert_allclose(md, core.mean_density(p, got), rtol=1e-13)
+    np.testing.assert_allclose(md, core.mean_density(p, ref), rtol=tol)

@@ -30,3 +30,20 @@ def test_growth_fit_recovers_exponent():
     assert ge == pytest.approx(g, rel=1e-10)
     assert gk == pytest.approx(g, rel=1e-10)
     assert fit.window(401) == slice(101, 401)
+
+
+def test_mean_density_profile_by_brute_force_and_mass():
+    # the averaged density profile (Sec. IV.A): the mean of rho = sum_q f_q
+    # along the interface direction x, row by row
+    rng = np.random.default_rng(21)
+    p = core.Params(nx=13, ny=7, dx=0.01, dy=0.01, dt=1e-5, tau=1e-5)
+    f = 0.05 + rng.random((19, p.ny, p.nx))
+    md = core.mean_density(p, f)
+    brute = np.array([sum(sum(f[q, j, i] for q in range(19)) for i in range(p.nx)) / p.nx for j in range(p.ny)])
+    np.testing.assert_allclose(md, brute, rtol=1e-15)
+    np.testing.assert_allclose(md, core.fields(p, f)[0].mean(axis=1), rtol=1e-14)
+    # nx times its sum is the mass of the state
+    assert md.sum() * p.nx == pytest.approx(core.diag(p, f)[0], rel=1e-14)
+    # a state uniform along x gives back its rows (to the rounding of nx equal terms over nx)
+    g = np.repeat(f[:, :, :1], p.nx, axis=2)
+    np.testing.assert_allclose(core.mean_density(p, g), g[:, :, 0].sum(axis=0), rtol=1e-15)
