@@ -290,6 +290,8 @@ def run_ours(args):
         line["roofline_hbm"] = hbm_roof
     if rank == 0 and not args.no_sweep:
         line["sweep"] = sweep_measure(args.sweep_steps, torch)
+    if rank == 0 and not args.no_physics:
+        line["paper_sweeps"] = physics_measure(torch)
     if rank == 0 and not args.no_schemes:
         line["schemes"] = schemes_measure(args.workload, 100, torch)
     if rank == 0 and not args.no_adjoint:
@@ -403,6 +405,33 @@ def adjoint_measure(prec: str, steps: int, torch):
             "speedup_vs_full_storage": round(t_full / t_ckpt, 3),
             "checkpoint_mb": round(((steps + 44) // 45) * state_mb, 1),
             "full_storage_mb": round(steps * state_mb, 1)}
+
+
+def physics_measure(torch):
+    """The paper's three Kelvin-Helmholtz sweeps (Sec. IV) on the batched
+    engine (paper_1010_4124_gb300.sweeps): growth rates, the fitted laws of
+    the paper's Figs. 7 and 9, and the batched throughput of each sweep."""
+    from paper_1010_4124_gb300 import sweeps
+    out = {"steps": 40000, "sample_every": 50, "paper": {"a": 2.70, "b": 0.07, "c": 5.28, "e": 0.62}}
+    for name in ("velocity", "density", "hybrid"):
+        pbs = sweeps.problems(name)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = sweeps.run(name)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        cells = sum(pb.nx * pb.ny for pb in pbs)
+        rec = {"instances": len(pbs), "state": sweeps.SWEEPS[name][0], "seconds": round(dt, 3),
+               "gcell_s": round(cells * 40000 / dt / 1e9, 3),
+               "gamma": [[r["Dv"], r["Drho"], round(r["gamma"], 4)] for r in res]}
+        if name == "velocity":
+            a, b = sweeps.fit_velocity_law(res)
+            rec["fit_a_b"] = [round(a, 4), round(b, 5)]
+        if name == "density":
+            c, e = sweeps.fit_density_law(res)
+            rec["fit_c_e"] = [round(c, 4), round(e, 4)]
+        out[name] = rec
+    return out
 
 
 SOD_P_STAR = 0.285975  # star pressure of the gamma = 2 Sod problem (exact Riemann solution)
@@ -551,6 +580,7 @@ def main():
     ap.add_argument("--sweep-steps", type=int, default=280)
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-schemes", action="store_true")
+    ap.add_argument("--no-physics", action="store_true")
     ap.add_argument("--adjoint-steps", type=int, default=2000)
     args = ap.parse_args()
     if args.warmup < 3:

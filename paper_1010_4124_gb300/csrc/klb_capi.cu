@@ -197,7 +197,7 @@ int klb_create(const klb_params* pin, klb_t** out) {
     const double cfl = vmax * p.dt / std::min(p.dx, p.dy);
     if (p.dt / p.tau > 2.0)
         fprintf(stderr, "klb: warning: dt/tau = %g > 2 (the BGK factor 1 - dt/tau exceeds -1)\n", p.dt / p.tau);
-    if (cfl > 0.03)
+    if (cfl > 0.03 * (1 + 1e-9))
         fprintf(stderr, "klb: warning: CFL max(v) dt/min(dx,dy) = %g > 0.03; forward Euler + WENO5 may grow\n", cfl);
 
     klb_t* h = new klb();

@@ -58,6 +58,7 @@ class Problem:
     amp: float = 0.01
     modes: int = 1
     phase_seed: int | None = None
+    envelope: str = "gauss"  # cross-stream envelope of u_y: "gauss" exp(-(y/(0.05 Ly))^2), "exp" exp(-k|y|)
 
     def with_(self, **kw) -> "Problem":
         return replace(self, **kw)
@@ -90,6 +91,29 @@ def khi(nx: int = 512, ny: int = 512, steps: int = 4000, Dv: float = 4.0, Drho: 
 def roofline_4096(steps: int = 1000) -> Problem:
     """The 4096 x 4096 KHI: D_v = D_rho = 16 cells, four modes of seeded phase."""
     return khi(4096, 4096, steps, Dv=16.0, Drho=16.0, modes=4, phase_seed=ROOFLINE_PHASE_SEED)
+
+
+def paper_khi(Dv: float, Drho: float, state: str = "A", steps: int = 40000, sample_every: int = 50) -> Problem:
+    """The paper's Kelvin-Helmholtz set-ups (Sec. IV) in this library's
+    orientation (the interface along x, periodic; the cross-stream direction y,
+    outflow).  Domain 0.2 (periodic, the paper's height) x 0.6 (cross-stream,
+    the paper's length); dt = tau = 1e-5; perturbation
+    u_y = 0.02 sin(k x) exp(-k |y|), k = 10 pi (one wavelength over the
+    periodic length).  D_v, D_rho in cells.
+      state "A" (Sec. IV.A, the velocity-gradient study): rho 5.0 / 2.0,
+        u_x +-0.5, p = 2.5, dx = dy = 0.001 (200 x 600 cells);
+      state "B" (Sec. IV.B, the density-gradient study, and the hybrid
+        R = D_rho / D_v study of Sec. IV.C): rho 5.0 / 1.25, u_x +-0.5,
+        p = 1.5, dx = dy = 0.002 (100 x 300 cells)."""
+    if state == "A":
+        nx, ny, d, rho2, p0 = 200, 600, 0.001, 2.0, 2.5
+    elif state == "B":
+        nx, ny, d, rho2, p0 = 100, 300, 0.002, 1.25, 1.5
+    else:
+        raise ValueError(f"unknown state {state}")
+    return Problem(f"khi-{state}", nx, ny, d, d, 1e-5, 1e-5, steps, bc_x=("periodic", "periodic"),
+                   bc_y=("outflow", "outflow"), sample_every=sample_every, Dv=float(Dv), Drho=float(Drho),
+                   rho1=5.0, rho2=rho2, u0=1.0, p0=p0, amp=0.02, modes=1, envelope="exp")
 
 
 def sweep_instances(steps: int = 2000, seed: int = SWEEP_SEED):
@@ -126,7 +150,10 @@ def perturbation_shape(pb: Problem):
     """u_y of the initial state (the field the adjoint differentiates against)."""
     X, Y = coords(pb)
     Lx, Ly = pb.nx * pb.dx, pb.ny * pb.dy
-    env = np.exp(-(Y / (0.05 * Ly)) ** 2)
+    if pb.envelope == "exp":  # exp(-k |y|) with k = 2 pi / Lx, the wave number of the first mode
+        env = np.exp(-(2.0 * np.pi / Lx) * np.abs(Y))
+    else:
+        env = np.exp(-(Y / (0.05 * Ly)) ** 2)
     uy = np.zeros_like(X)
     for m, ph in enumerate(phases(pb), start=1):
         uy = uy + pb.amp * np.sin(2.0 * np.pi * m * X / Lx + ph) * env
