@@ -44,6 +44,12 @@ BYTES_PER_NODE = {"fp32": 152, "fp64": 304}  # 19 reads + 19 writes per node-upd
 FP32_OPS_PER_NODE = 1377
 # FP32 issue peak of the FMA pipes: 152 SMs x 128 lanes x 2070 MHz (max SM clock)
 FP32_LANE_PEAK_T = 152 * 128 * 2.070e9 / 1e12
+# FP64 path (the parity path, every operation rounded as the oracle rounds it):
+# FP64-pipe instructions per node-update counted by ncu (DADD + DMUL + DFMA,
+# the division sequences included; profiles/step_fp64_khi512_ncu.md), and the
+# FP64 pipe peak: 152 SMs x 2 per clock x 2070 MHz
+FP64_OPS_PER_NODE = 5214
+FP64_PEAK_T = 152 * 2 * 2.070e9 / 1e12
 STEP_KERNEL_SOURCES = ["paper_1010_4124_gb300/csrc/klb_step_f32.cuh", "paper_1010_4124_gb300/csrc/klb_step_f32.cu",
                        "paper_1010_4124_gb300/csrc/klb_device.cuh"]
 
@@ -230,13 +236,19 @@ def run_ours(args):
     hbm_roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_kind": peak_kind, "traffic": traffic,
                 "algorithmic_bytes_per_node": BYTES_PER_NODE[prec], "kernel": kernel}
-    alu_roof = None
     if prec == "fp32":
         ops = FP32_OPS_PER_NODE * cells / (per_step_ms * 1e-3) / 1e12
         alu_roof = {"bound": "alu", "achieved": round(ops, 2), "peak": round(FP32_LANE_PEAK_T, 2),
                     "unit": "T FP32 lane-ops/s (fma = 1)", "frac": round(ops / FP32_LANE_PEAK_T, 4),
                     "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz",
                     "traffic": traffic, "ops_per_node": FP32_OPS_PER_NODE, "kernel": kernel}
+    else:
+        ops = FP64_OPS_PER_NODE * cells / (per_step_ms * 1e-3) / 1e12
+        alu_roof = {"bound": "alu", "achieved": round(ops, 4), "peak": round(FP64_PEAK_T, 4),
+                    "unit": "T FP64 pipe instructions/s", "frac": round(ops / FP64_PEAK_T, 4),
+                    "peak_kind": "derived: 152 SMs x 2 FP64 per clock x 2070 MHz",
+                    "traffic": traffic, "ops_per_node": FP64_OPS_PER_NODE,
+                    "ops_kind": "executed per node, counted by ncu", "kernel": kernel}
 
     # ---- end to end through the C ABI with host buffers (pinned)
     pin = [torch.from_numpy(a).pin_memory() for a in fields]
@@ -283,11 +295,10 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clocks,
     }
-    if alu_roof is not None:
-        # the FP32 step is bound by FP32 issue, not by HBM: the ALU roofline
-        # is the binding one, the HBM fraction is reported beside it
-        line["roofline"] = alu_roof
-        line["roofline_hbm"] = hbm_roof
+    # both steps are bound by their arithmetic units, not by HBM: the ALU
+    # roofline is the binding one, the HBM fraction is reported beside it
+    line["roofline"] = alu_roof
+    line["roofline_hbm"] = hbm_roof
     if rank == 0 and not args.no_sweep:
         line["sweep"] = sweep_measure(args.sweep_steps, torch)
     if rank == 0 and not args.no_physics:
