@@ -1,5 +1,6 @@
-// klb_step.cuh -- the fused FDLB time step for sm_103a (kernel template;
-// klb_step_f32.cu and klb_step_f64.cu instantiate it).
+// klb_step.cuh -- the fused FDLB time step in FP64, the parity path
+// (instantiated by klb_step_f64.cu; the FP32 production step is
+// klb_step_f32.cuh).
 //
 // One launch = one forward-Euler step (Eq. 47 of arXiv:1010.4124) over the
 // whole grid.  Each CTA owns a TX x TY tile of interior nodes:
@@ -10,7 +11,7 @@
 //   2. each thread takes the 19 values of its node, forms rho, u, T
 //      (Eq. 10), F_k(T) (Eqs. 44-46) and the equilibrium factors (Eq. 28);
 //   3. for every velocity q (unrolled; upwind side fixed at compile time),
-//      each thread computes the WENO5 flux of its left x-face and bottom
+//      each thread computes the face flux (WENO5, or the scheme chosen) of its left x-face and bottom
 //      y-face from shared memory, two warps compute the tile's right and top
 //      edge faces, the faces go through shared memory, and each thread forms
 //      the flux divergence, the BGK term and the new value, storing it
@@ -27,10 +28,6 @@ namespace fdlb {
 
 template <typename T>
 struct StepTile;
-template <>
-struct StepTile<float> {
-    static constexpr int TX = 32, TY = 16;
-};
 template <>
 struct StepTile<double> {
     static constexpr int TX = 32, TY = 8;
@@ -92,11 +89,11 @@ __device__ __forceinline__ void velocity_update(const StepConst<T>& c, const Geo
     using L = SmemLayout<T, TX, TY>;
     constexpr int SX = L::SX;
     constexpr int SGX = sgn_x(Q), SGY = sgn_y(Q);
-    constexpr bool F32 = std::is_same<T, float>::value;
+    static_assert(std::is_same<T, double>::value, "the FP32 step is klb_step_f32.cuh");
     const T* P = tile + Q * L::PLANE;
     const int sx = tx + 4, sy = ty + 3;
     const int tid = threadIdx.x;
-    const T epsx = F32 ? c.ex[Q] : c.eps, epsy = F32 ? c.ey[Q] : c.eps;
+    const T epsx = c.eps, epsy = c.eps;
     T hl = 0, hb = 0;
     if (SGX != 0) {
         hl = face_x<T, SX, SGX>(P, sy, sx, c.vx[Q], epsx, c.scheme);
@@ -113,19 +110,10 @@ __device__ __forceinline__ void velocity_update(const StepConst<T>& c, const Geo
         hx[r * (TX + 1) + TX] = face_x<T, SX, SGX>(P, r + 3, TX + 4, c.vx[Q], epsx, c.scheme);
     }
     __syncthreads();
-    T fn;
-    if constexpr (F32) {
-        // fq is the post-collision value; subtract the flux divergence
-        T div = 0;
-        if (SGX != 0) div += c.cx[Q] * (hx[ty * (TX + 1) + tx + 1] - hl);
-        if (SGY != 0) div += c.cy[Q] * (hy[(ty + 1) * TX + tx] - hb);
-        fn = fq - div;
-    } else {
-        // Eq. (47) as written: f - dt (dh_x/dx + dh_y/dy) - (dt/tau)(f - f^(0))
-        const T dhx = SGX != 0 ? hx[ty * (TX + 1) + tx + 1] - hl : T(0);
-        const T dhy = SGY != 0 ? hy[(ty + 1) * TX + tx] - hb : T(0);
-        fn = fq - c.dt * (dhx / c.dx + dhy / c.dy) - c.relax * (fq - Arith<T>::feq(c, s, Q));
-    }
+    // Eq. (47) as written: f - dt (dh_x/dx + dh_y/dy) - (dt/tau)(f - f^(0))
+    const T dhx = SGX != 0 ? hx[ty * (TX + 1) + tx + 1] - hl : T(0);
+    const T dhy = SGY != 0 ? hy[(ty + 1) * TX + tx] - hb : T(0);
+    const T fn = fq - c.dt * (dhx / c.dx + dhy / c.dy) - c.relax * (fq - Arith<T>::feq(c, s, Q));
     if (active) store_with_images(out, g, Q, ix, iy, fn);
     __syncthreads();
 }
@@ -199,7 +187,6 @@ __global__ void __launch_bounds__(TX* TY) step_kernel(const __grid_constant__ CU
         diag_block_reduce<TX * TY>(v, diag_partials + 8ll * (blockIdx.y * gridDim.x + blockIdx.x));
     }
 
-    if constexpr (std::is_same<T, float>::value) Arith<T>::collide(c, s, f);  // f <- post-collision values
     VelLoop<T, TX, TY, 0>::run(c, g, tile, hx, hy, s, f, tx, ty, ix, iy, active, out);
 }
 
