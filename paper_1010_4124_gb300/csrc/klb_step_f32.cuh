@@ -166,6 +166,7 @@ __device__ __forceinline__ void pass_a_xy(const StepConst<float>& c, const float
     float hr = __shfl_down_sync(0xffffffffu, h.x, 1);
     if (lane == 31) hr = edge[Q - 1];  // the tile's right edge face
     post[Q] = fmaf(-c.cx[Q], __fsub_rn(hr, h.x), post[Q]);
+    post[Q] = fmaf(c.cy[Q], h.y, post[Q]);  // the face below enters now, the face above after the barrier
     yf[(yslot(Q) * (TY + 1) + ty) * 32 + lane] = h.y;
 }
 // pass A for two velocities QA, QB with an x component only
@@ -363,13 +364,10 @@ __global__ void __launch_bounds__(32 * TY, 16 / TY) step_f32_kernel(const __grid
             __syncthreads();
             return;
         }
-        // y fluxes from the faces below and above each node
+        // y fluxes: the face above each node (its upper neighbour's lower face)
 #pragma unroll
         for (int q = 1; q < NQ; ++q) {
-            if (sgn_y(q) != 0) {
-                const float* col = yf + (yslot(q) * (TY + 1) + ty) * 32 + lane;
-                f[q] = fmaf(-c.cy[q], __fsub_rn(col[32], col[0]), f[q]);
-            }
+            if (sgn_y(q) != 0) f[q] = fmaf(-c.cy[q], yf[(yslot(q) * (TY + 1) + ty + 1) * 32 + lane], f[q]);
         }
         if (active) {
             float* o = out + (long long)(iy + GY) * g.px + (ix + GX);
