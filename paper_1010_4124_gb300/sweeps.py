@@ -68,6 +68,7 @@ def run_pairs(state: str, pairs, steps: int = 40000, sample_every: int = 50, str
     with klb.KlbBatch.from_problems(pbs, stream=stream) as bt:
         for m, pb in zip(bt.members, pbs):
             m.init_fields(*inputs.fields(pb))
+        bt.autotune(steps=5)  # picks the tile shape on a snapshot and restores the state
         bt.step(steps)
         bt.sync()
         diags = [m.diagnostics(cap=steps // sample_every + 1) for m in bt.members]

@@ -343,3 +343,26 @@ def test_mean_density_profile(prec, tol):
         np.testing.assert_array_equal(dev.cpu().numpy(), md)
     np.testing.assert_allclose(md, core.mean_density(p, got), rtol=1e-13)
     np.testing.assert_allclose(md, core.mean_density(p, ref), rtol=tol)
+
+
+@pytest.mark.parametrize("bcx,bcy", BCS)
+@pytest.mark.parametrize("nx,ny", SIZES + [(28, 16), (29, 17), (60, 33)])
+def test_fp32_one_step_parity_every_size(nx, ny, bcx, bcy):
+    # one FP32 step from rough data, both tile shapes, against the FP64 oracle
+    # on the scale of f: grids narrower than one tile, exactly one tile (28 + 4
+    # ghost columns = 32), ragged last tiles in x and y, every boundary kind
+    pb = _problem(nx, ny, bcx, bcy)
+    p = oracle_params(pb)
+    fields = inputs.rough_random_fields(nx, ny, seed=nx * 7 + ny)
+    f0 = perturbed_state(pb, fields, seed=5)
+    ref = core.step(p, f0, fixed=core.fixed_ghosts(p, *fields))
+    got = []
+    for v in (0, 1):
+        with gpu_handle(pb, "fp32") as h:
+            h.variant = v
+            h.init_fields(*[np.ascontiguousarray(a) for a in fields])
+            h.set_f(np.ascontiguousarray(f0))
+            h.step(1)
+            got.append(h.get_f())
+    assert np.array_equal(got[0], got[1])
+    assert rel_err_global(got[0], ref) <= 2e-6
