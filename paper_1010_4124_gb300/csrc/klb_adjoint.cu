@@ -86,16 +86,15 @@ static int vjp_step(klb_adj_t* a, const void* f, const void* lam_in, void* lam_o
     const Geom& g = h->g;
     // one thread per (face, velocity) and per (node, velocity)
     const long long n = (long long)g.nx * g.ny;
-    adj_faces_x_kernel<T><<<dim3(grid_of((long long)(g.nx + 1) * g.ny), NQ - 1), 256, 0, h->stream>>>(
-        c, g, (const T*)f, (const T*)lam_in, (T*)a->Dx);
-    adj_faces_y_kernel<T><<<dim3(grid_of((long long)g.nx * (g.ny + 1)), 12), 256, 0, h->stream>>>(
-        c, g, (const T*)f, (const T*)lam_in, (T*)a->Dy);
+    const long long nfmax = std::max((long long)(g.nx + 1) * g.ny, (long long)g.nx * (g.ny + 1));
+    adj_faces_kernel<T><<<dim3(grid_of(nfmax), (NQ - 1) + 12), 256, 0, h->stream>>>(
+        c, g, (const T*)f, (const T*)lam_in, (T*)a->Dx, (T*)a->Dy);
     adj_node_kernel<T><<<grid_of(n), 256, 0, h->stream>>>(c, g, (const T*)f, (const T*)lam_in, (T*)a->Nb);
     adj_gather_kernel<T><<<dim3(grid_of(n), NQ), 256, 0, h->stream>>>(
         c, g, (const T*)lam_in, (const T*)a->Nb, (const T*)a->Dx, (const T*)a->Dy, T(coef), (T*)lam_out);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return afail(a, KLB_E_CUDA, std::string("adjoint kernels: ") + cudaGetErrorString(e));
-    h->launches += 4;
+    h->launches += 3;
     return KLB_OK;
 }
 

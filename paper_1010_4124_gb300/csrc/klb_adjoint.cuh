@@ -21,13 +21,19 @@
 
 namespace fdlb {
 
+// 1/x: correctly rounded in FP64 (the accuracy reference of the adjoint), the
+// hardware approximation in FP32 (the FP32 adjoint is checked against the FP64
+// one to 2e-3)
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+__device__ __forceinline__ float recip(float x) { return rcp_approx(x); }
+
 // F_k(T) and dF_k/dT for k = 0..3 (Eqs. 44-46 and their derivative)
 template <typename T>
 __device__ __forceinline__ void coeffs_and_slope(const StepConst<T>& c, T Tm, T F[4], T dF[4]) {
     T s = 0, ds = 0;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const T id = T(1) / c.den[k];
+        const T id = recip(c.den[k]);
         F[k + 1] = (T(24) * Tm * Tm * Tm - c.a4[k] * Tm * Tm + c.pk[k] * Tm) * id;
         dF[k + 1] = (T(72) * Tm * Tm - T(2) * c.a4[k] * Tm + c.pk[k]) * id;
         s += F[k + 1];
@@ -56,9 +62,9 @@ __device__ __forceinline__ T weno5_grad(T a, T b, T c, T d, T e, T eps, T g[5]) 
     const T s2 = eps + k13 * t2 * t2 + T(0.25) * r2 * r2;
     const T s3 = eps + k13 * t3 * t3 + T(0.25) * r3 * r3;
     // one reciprocal per indicator and one for the sum of the alphas
-    const T i1 = T(1) / s1, i2 = T(1) / s2, i3 = T(1) / s3;
+    const T i1 = recip(s1), i2 = recip(s2), i3 = recip(s3);
     const T al1 = T(0.1) * i1 * i1, al2 = T(0.6) * i2 * i2, al3 = T(0.3) * i3 * i3;
-    const T iS = T(1) / (al1 + al2 + al3);
+    const T iS = recip(al1 + al2 + al3);
     const T w1 = al1 * iS, w2 = al2 * iS, w3 = al3 * iS;
     const T h = w1 * h1 + w2 * h2 + w3 * h3;
     const T b1 = -T(2) * w1 * (h1 - h) * i1;
@@ -95,7 +101,7 @@ __device__ __forceinline__ Mom<T> moments_of(const StepConst<T>& c, const T* f) 
         e += f[q] * c.v2[q];
     }
     Mom<T> m;
-    const T ir = T(1) / r;
+    const T ir = recip(r);
     m.rho = r;
     m.ux = jx * ir;
     m.uy = jy * ir;
@@ -112,7 +118,7 @@ __device__ __forceinline__ void feq_vjp_fields(const StepConst<T>& c, T rho, T u
     T F[4], dF[4];
     coeffs_and_slope(c, Tm, F, dF);
     const T u2 = ux * ux + uy * uy;
-    const T iT = T(1) / Tm;  // the only division
+    const T iT = recip(Tm);  // the only reciprocal of the loop
     const T A = T(1) - T(0.5) * u2 * iT;
     T gr = 0, gx = 0, gy = 0, gT = 0;
 #pragma unroll
@@ -140,7 +146,7 @@ template <typename T>
 __device__ __forceinline__ void feq_vjp_moments(const StepConst<T>& c, const Mom<T>& m, const T* lam, T g[4]) {
     T G[4];
     feq_vjp_fields(c, m.rho, m.ux, m.uy, m.Tm, lam, G);
-    const T ir = T(1) / m.rho;
+    const T ir = recip(m.rho);
     const T u2 = m.ux * m.ux + m.uy * m.uy;
     g[0] = G[0] - G[1] * m.ux * ir - G[2] * m.uy * ir + G[3] * (-m.E * ir * ir + u2 * ir);
     g[1] = (G[1] - G[3] * m.ux) * ir;
@@ -178,10 +184,10 @@ __device__ __forceinline__ int yslot_of(int q) {
 // of row j, for velocity q = blockIdx.y + 1 (every moving velocity has
 // v_x != 0): the five entries mu * v * dh/dF.
 template <typename T>
-__global__ void adj_faces_x_kernel(const StepConst<T> c, const Geom g, const T* __restrict__ f,
-                                   const T* __restrict__ lam, T* __restrict__ D) {
+__device__ __forceinline__ void adj_faces_x(const StepConst<T>& c, const Geom& g, const T* __restrict__ f,
+                                            const T* __restrict__ lam, T* __restrict__ D, int qx) {
     const long long nf = (long long)(g.nx + 1) * g.ny;
-    const int qx = blockIdx.y, q = qx + 1;
+    const int q = qx + 1;
     const T v = c.vx[q];
     T* __restrict__ out = D + (long long)(5 * qx) * nf;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nf; t += (long long)gridDim.x * blockDim.x) {
@@ -204,10 +210,10 @@ __global__ void adj_faces_x_kernel(const StepConst<T> c, const Geom g, const T* 
 // y faces: thread t = (i, j), j in [0, ny] the face between rows j-1 and j of
 // column i, for the velocity of y slot blockIdx.y
 template <typename T>
-__global__ void adj_faces_y_kernel(const StepConst<T> c, const Geom g, const T* __restrict__ f,
-                                   const T* __restrict__ lam, T* __restrict__ D) {
+__device__ __forceinline__ void adj_faces_y(const StepConst<T>& c, const Geom& g, const T* __restrict__ f,
+                                            const T* __restrict__ lam, T* __restrict__ D, int qy) {
     const long long nf = (long long)g.nx * (g.ny + 1);
-    const int qy = blockIdx.y, q = yvel_of(qy);
+    const int q = yvel_of(qy);
     const T v = c.vy[q];
     T* __restrict__ out = D + (long long)(5 * qy) * nf;
     const long long P = g.px;
@@ -228,6 +234,15 @@ __global__ void adj_faces_y_kernel(const StepConst<T> c, const Geom g, const T* 
 #pragma unroll
         for (int k = 0; k < 5; ++k) out[k * nf + t] = mu * gr[k];
     }
+}
+
+// all face gradients in one launch: blockIdx.y < 18 the x faces of velocity
+// blockIdx.y + 1, else the y faces of y slot blockIdx.y - 18
+template <typename T>
+__global__ void adj_faces_kernel(const StepConst<T> c, const Geom g, const T* __restrict__ f,
+                                 const T* __restrict__ lam, T* __restrict__ Dx, T* __restrict__ Dy) {
+    if (blockIdx.y < NQ - 1) adj_faces_x(c, g, f, lam, Dx, (int)blockIdx.y);
+    else adj_faces_y(c, g, f, lam, Dy, (int)blockIdx.y - (NQ - 1));
 }
 
 // Per node: the sensitivity of f^(0) carried to the moments (four values,
