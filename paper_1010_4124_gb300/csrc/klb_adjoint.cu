@@ -148,6 +148,7 @@ static int reverse(klb_adj_t* a, bool sources, double g_ke, double g_gamma, int*
     klb_t* h = a->h;
     int lc = *lam_cur;
     for (int s = a->nck - 1; s >= 0; --s) {
+        fdlb::NvtxRange trace_("klb_adjoint segment");
         const int64_t n0 = (int64_t)s * a->ckpt;
         const int64_t n1 = std::min<int64_t>(n0 + a->ckpt, a->nsteps);
         const int len = (int)(n1 - n0);
@@ -271,6 +272,7 @@ klb_t* klb_adjoint_grid(klb_adj_t* a) { return a ? a->h : nullptr; }
 
 int klb_adjoint_forward(klb_adj_t* a, const double* rho, const double* ux, const double* uy, const double* T,
                         int on_device, double* ke, double* gamma) {
+    fdlb::NvtxRange trace_("klb_adjoint_forward");
     if (!a || !rho || !ux || !uy || !T) return a ? afail(a, KLB_E_INVAL, "NULL argument") : KLB_E_INVAL;
     klb_t* h = a->h;
     const size_t nn = (size_t)h->g.nx * h->g.ny;
@@ -319,6 +321,7 @@ int klb_adjoint_forward(klb_adj_t* a, const double* rho, const double* ux, const
 
 int klb_adjoint_backward(klb_adj_t* a, double g_ke, double g_gamma, double* d_rho, double* d_ux, double* d_uy,
                          double* d_T, int on_device) {
+    fdlb::NvtxRange trace_("klb_adjoint_backward");
     if (!a || !d_rho || !d_ux || !d_uy || !d_T) return a ? afail(a, KLB_E_INVAL, "NULL argument") : KLB_E_INVAL;
     if (!a->forward_done) return afail(a, KLB_E_STATE, "klb_adjoint_backward before klb_adjoint_forward");
     klb_t* h = a->h;
@@ -347,6 +350,7 @@ int klb_adjoint_backward(klb_adj_t* a, double g_ke, double g_gamma, double* d_rh
 }
 
 int klb_adjoint_vjp(klb_adj_t* a, const double* lam_N, double* lam_0, int on_device) {
+    fdlb::NvtxRange trace_("klb_adjoint_vjp");
     if (!a || !lam_N || !lam_0) return a ? afail(a, KLB_E_INVAL, "NULL argument") : KLB_E_INVAL;
     if (!a->forward_done) return afail(a, KLB_E_STATE, "klb_adjoint_vjp before klb_adjoint_forward");
     klb_t* h = a->h;

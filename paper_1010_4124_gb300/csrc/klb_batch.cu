@@ -241,6 +241,7 @@ klb_t* klb_batch_member(klb_batch_t* b, int i) {
 }
 
 int klb_batch_step(klb_batch_t* b, int64_t n) {
+    fdlb::NvtxRange trace_("klb_batch_step");
     if (!b) return KLB_E_INVAL;
     if (n < 0) return bfail(b, KLB_E_INVAL, "negative step count");
     int r = same_state(b);
@@ -314,6 +315,7 @@ int klb_batch_use_graph(klb_batch_t* b, int on) {
 }
 
 int klb_batch_autotune(klb_batch_t* b, int steps, int* variant) {
+    fdlb::NvtxRange trace_("klb_batch_autotune");
     if (!b || steps < 1) return b ? bfail(b, KLB_E_INVAL, "steps must be >= 1") : KLB_E_INVAL;
     int r = same_state(b);
     if (r != KLB_OK) return r;

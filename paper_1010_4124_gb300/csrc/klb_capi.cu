@@ -319,6 +319,7 @@ static int stage_fields(klb_t* h, const double* rho, const double* ux, const dou
 
 int klb_init_fields(klb_t* h, const double* rho, const double* ux, const double* uy, const double* T,
                     int on_device) {
+    fdlb::NvtxRange trace_("klb_init_fields");
     if (!h) return KLB_E_INVAL;
     const double* d[4];
     int r = stage_fields(h, rho, ux, uy, T, on_device, d);
@@ -474,6 +475,7 @@ static int one_step(klb_t* h) {
 extern "C" {
 
 int klb_step(klb_t* h, int64_t n) {
+    fdlb::NvtxRange trace_("klb_step");
     if (!h) return KLB_E_INVAL;
     if (n < 0) return fail(h, KLB_E_INVAL, "negative step count");
     if (!h->initialized) return fail(h, KLB_E_STATE, "klb_step before klb_init_fields");
@@ -513,6 +515,7 @@ static int read_nsamples(klb_t* h, long long* n) {
 extern "C" {
 
 int klb_moments(klb_t* h, double* rho, double* ux, double* uy, double* T, int on_device) {
+    fdlb::NvtxRange trace_("klb_moments");
     if (!h) return KLB_E_INVAL;
     if (!h->initialized) return fail(h, KLB_E_STATE, "klb_moments before klb_init_fields");
     const size_t n = (size_t)h->g.nx * h->g.ny;
@@ -547,6 +550,7 @@ int klb_mean_density(klb_t* h, double* out, int on_device) {
 }
 
 int klb_diagnostics(klb_t* h, double* out, int64_t cap, int64_t* count) {
+    fdlb::NvtxRange trace_("klb_diagnostics");
     if (!h || !count || (cap > 0 && !out)) return h ? fail(h, KLB_E_INVAL, "NULL argument") : KLB_E_INVAL;
     if (!h->initialized) return fail(h, KLB_E_STATE, "klb_diagnostics before klb_init_fields");
     int r = flush_sample(h);

@@ -7,6 +7,7 @@
 #include <string>
 
 #include "../../include/klb.h"
+#include <nvtx3/nvToolsExt.h>
 #include "klb_launch.h"
 
 using fdlb::Geom;
@@ -45,6 +46,15 @@ struct klb {  // state of one grid
 };
 
 namespace fdlb {
+
+// Tracing: an NVTX range (visible to Nsight tools; no cost without one) over
+// one call of the library's public API.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 // the step constants of a problem statement, in either arithmetic type
 void step_constants(const klb_params& p, StepConst<float>& c);
 void step_constants(const klb_params& p, StepConst<double>& c);
