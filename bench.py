@@ -146,6 +146,24 @@ def workload_problem(name: str, steps: int):
     return pb
 
 
+def max_over_ranks(x: float, ws: int, device: str = "cuda") -> float:
+    """The largest value of x over the ranks (the job's time is its slowest
+    replica's); x itself when the job has one rank."""
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(cells: int, steps: int, ws: int, seconds: float) -> float:
+    """Whole-job Gcell-updates/s of ws replicas of one grid each (weak scaling):
+    the units all ranks processed over the slowest rank's time."""
+    return cells * steps * ws / seconds / 1e9
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -219,14 +237,10 @@ def run_ours(args):
     launches = h.launch_count - n0
     ms = e0.elapsed_time(e1)
     clocks = clk.summary()
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, ws)
     cells = pb.nx * pb.ny
     state_gb = NQ * pb.ny * pb.nx * (4 if prec == "fp32" else 8) / 1e9
-    value = cells * args.steps * ws / (ms * 1e-3) / 1e9
+    value = job_rate(cells, args.steps, ws, ms * 1e-3)
     per_step_ms = ms / args.steps
     achieved = BYTES_PER_NODE[prec] * cells / (per_step_ms * 1e-3) / 1e9  # GB/s
     peak, peak_kind = measured_peaks()
@@ -262,11 +276,7 @@ def run_ours(args):
     h.moments(tuple(o.numpy() for o in outs))  # synchronises
     t1 = time.perf_counter()
     e2e_s = t1 - t0
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, ws)
     h.close()
 
     line = {
@@ -289,7 +299,7 @@ def run_ours(args):
                    "l2": f"inputs larger than L2 (2 x {state_gb:.2f} GB of f per step, L2 129 MB)",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "roofline": hbm_roof,
-        "e2e": {"value": round(cells * args.steps * ws / e2e_s / 1e9, 4), "unit": "Gcell-updates/s",
+        "e2e": {"value": round(job_rate(cells, args.steps, ws, e2e_s), 4), "unit": "Gcell-updates/s",
                 "h2d_bytes_per_step": round(4 * 8 * cells / args.steps, 1),
                 "d2h_bytes_per_step": round(4 * 8 * cells / args.steps, 1)},
         "gpu_launches": launches,
