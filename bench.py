@@ -13,7 +13,15 @@ Prints ONE JSON line (rank 0):
   e2e     the same metric through the C ABI with host buffers: klb_init_fields
           from pinned host fields, the steps, klb_moments back to pinned host
           memory, all inside the timed region
-  roofline, cpu_baseline, clocks, gpu_launches.
+  roofline      the binding roofline of the step kernel: FP32 (or FP64)
+                operations per node-update x rate, against the ALU peak
+                (152 SMs x lanes x max clock); roofline_hbm beside it: 152
+                (304) algorithmic bytes per node-update x rate against the
+                measured copy bandwidth; traffic = ncu DRAM bytes per launch
+  cpu_baseline  the FP64 oracle on the host cores, on a band of the workload
+  clocks, gpu_launches, and the legs sweep (batched vs looped plain step),
+  adjoint (checkpointed reverse sweep), schemes (the convection schemes of
+  the paper's comparison) and paper_sweeps (its Kelvin-Helmholtz studies).
 
 --impl reference times the FP64 CPU oracle (the baseline of this method: the
 paper publishes no timings) on a bounded sample of the same workload.
