@@ -175,8 +175,8 @@ int klb_layout(const klb_t* h, const void** base, int64_t* pitch, int64_t* plane
  * library launched on its stream). */
 int64_t klb_launch_count(const klb_t* h);
 
-/* Kernel variant (tile shape) of the FP32 step: 0 = tiles of 31 x 16 nodes,
- * one CTA of 16 warps per SM; 1 = tiles of 31 x 8 nodes, two CTAs of 8 warps
+/* Kernel variant (tile shape) of the FP32 step: 0 = tiles of 32 x 16 nodes,
+ * one CTA of 16 warps per SM; 1 = tiles of 32 x 8 nodes, two CTAs of 8 warps
  * per SM.  Every node is computed by the same arithmetic in both, so the
  * states are bitwise identical; only the speed differs (the diagnostics sums
  * may differ in the last bits, being reduced in another order).  The FP64
@@ -304,7 +304,7 @@ const char* klb_adjoint_last_error(const klb_adj_t* a);
  * writes them to out[0..6], a DEVICE pointer owned by the caller.  f is a
  * device pointer to plane 0 of a distribution array in the library's layout
  * (as klb_layout reports it: element (q, j, i) of the interior at
- * f[q*plane + (j+3)*pitch + (i+4)], in the precision given, KLB_FP32 or
+ * f[q*plane + (j+gy)*pitch + (i+gx)], gx = 4, gy = 3, in the precision given, KLB_FP32 or
  * KLB_FP64); v are the ring speeds.  The work is enqueued on `stream` (NULL =
  * the default stream) and the call returns without waiting; it calls no
  * cudaMalloc, cudaFree or allocating library routine.  The sums are reduced
