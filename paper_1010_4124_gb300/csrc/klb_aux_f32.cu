@@ -8,8 +8,9 @@ KLB_AUX_INST(float)
 
 // One block folds all partial records, in record order per thread and a fixed
 // tree across threads.
-__global__ void diag_finalize_kernel(const double* __restrict__ partials, int nparts, double* __restrict__ ring,
-                                     int cap, long long* __restrict__ counter, int* __restrict__ err) {
+__device__ __forceinline__ void fold_records(const double* __restrict__ partials, int nparts,
+                                             double* __restrict__ ring, int cap, long long* __restrict__ counter,
+                                             int* __restrict__ err) {
     __shared__ double red[256][8];
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
@@ -40,6 +41,26 @@ __global__ void diag_finalize_kernel(const double* __restrict__ partials, int np
         *counter = n + 1;
         if (red[0][7] != 0.0) atomicOr(err, ERR_NONFINITE);
     }
+}
+
+__global__ void __launch_bounds__(256) diag_finalize_kernel(const double* __restrict__ partials, int nparts,
+                                                            double* __restrict__ ring, int cap,
+                                                            long long* __restrict__ counter, int* __restrict__ err) {
+    fold_records(partials, nparts, ring, cap, counter, err);
+}
+
+// the folds of the due members of a batch, one block each
+__global__ void __launch_bounds__(256) diag_finalize_batch_kernel(const DiagJob* __restrict__ jobs, DueMask due) {
+    const int j = blockIdx.x;
+    if (!((due.w[j >> 5] >> (j & 31)) & 1u)) return;  // uniform across the block
+    const DiagJob& J = jobs[j];
+    fold_records(J.partials, J.grid, J.ring, J.cap, J.counter, J.err);
+}
+
+cudaError_t launch_diag_finalize_batch(const DiagJob* jobs, int njobs, DueMask due, cudaStream_t s) {
+    if (njobs < 1) return cudaSuccess;
+    diag_finalize_batch_kernel<<<njobs, 256, 0, s>>>(jobs, due);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_diag_finalize(const double* partials, int nparts, double* ring, int cap, long long* counter,

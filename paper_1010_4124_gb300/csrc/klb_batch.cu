@@ -27,6 +27,8 @@ struct klb_batch {
     int ntiles = 0;                // tiles of one launch
     int variant = 0;
     int* err_dev = nullptr;        // error word of the batched step kernel
+    DiagJob* jobs_dev = nullptr;   // [2][n]: every member's sample of the state in buf[p]
+    int diag_ctas = 0;             // CTAs of one batched sample (all members)
     bool use_graph = true;
     int period = 0;                // steps per sampling period (graph unit)
     int graph_steps = 0;           // steps captured in one graph
@@ -80,6 +82,32 @@ static int upload(klb_batch_t* b) {
     }
     BCK(b, cudaMemcpy(b->descs_dev, d.data(), d.size() * sizeof(InstDesc), cudaMemcpyHostToDevice));
     b->ntiles = first;
+    // the members' stand-alone diagnostics, their CTAs laid end to end
+    std::vector<DiagJob> jb(2 * (size_t)n);
+    int cta = 0;
+    for (int i = 0; i < n; ++i) {
+        klb_t* h = b->m[i];
+        int tiles_x, nt;
+        f32_tiles(h->g.nx, h->g.ny, b->variant, &tiles_x, &nt);
+        const int grid = f32_grid(h->g.nx, h->g.ny, b->variant);
+        for (int p = 0; p < 2; ++p) {
+            DiagJob& j = jb[(size_t)p * n + i];
+            j.f = (const float*)h->buf[p];
+            j.g = h->g;
+            j.tiles_x = tiles_x;
+            j.ntiles = nt;
+            j.grid = grid;
+            j.first_cta = cta;
+            j.partials = h->diag_partials;
+            j.ring = h->diag_ring;
+            j.cap = h->cap;
+            j.counter = h->nsamp_dev;
+            j.err = h->err_dev;
+        }
+        cta += grid;
+    }
+    BCK(b, cudaMemcpy(b->jobs_dev, jb.data(), jb.size() * sizeof(DiagJob), cudaMemcpyHostToDevice));
+    b->diag_ctas = cta;
     drop_graphs(b);
     return KLB_OK;
 }
@@ -93,15 +121,35 @@ static int same_state(klb_batch_t* b) {
     return KLB_OK;
 }
 
+// the samples due on the members' current state: the records of every due
+// member in one launch, their folds in a second (each member's records and
+// fold are those of its own stand-alone diagnostics, hence the same bits)
+static int batch_sample(klb_batch_t* b) {
+    DueMask due;
+    memset(&due, 0, sizeof(due));
+    bool any = false;
+    for (size_t i = 0; i < b->m.size(); ++i)
+        if (b->m[i]->pending_sample) {
+            due.w[i >> 5] |= 1u << (i & 31);
+            any = true;
+        }
+    if (!any) return KLB_OK;
+    const int p = b->m[0]->cur;
+    const int n = (int)b->m.size();
+    const DiagJob* jobs = b->jobs_dev + (size_t)p * n;
+    cudaError_t e = launch_diag_f32_batch(b->m[0]->cf, jobs, n, b->diag_ctas, b->variant, due, b->stream);
+    if (e == cudaSuccess) e = launch_diag_finalize_batch(jobs, n, due, b->stream);
+    if (e != cudaSuccess) return bfail(b, KLB_E_CUDA, std::string("batched diagnostics: ") + cudaGetErrorString(e));
+    b->launches += 2;
+    for (klb_t* h : b->m) h->pending_sample = false;
+    return KLB_OK;
+}
+
 // one batched step: the samples that are due before it (the initial state),
 // the step of every member in one launch, then the samples due after it
 static int batch_step_once(klb_batch_t* b) {
-    for (klb_t* h : b->m) {
-        const int64_t before = h->launches;
-        int r = handle_sample_if_due(h);
-        if (r != KLB_OK) return bfail(b, r, h->err);
-        b->launches += h->launches - before;
-    }
+    int r = batch_sample(b);
+    if (r != KLB_OK) return r;
     const int p = b->m[0]->cur;
     const int n = (int)b->m.size();
     klb_t* h0 = b->m[0];
@@ -109,14 +157,8 @@ static int batch_step_once(klb_batch_t* b) {
                                     h0->spin_limit, h0->inject, b->variant, b->stream);
     if (e != cudaSuccess) return bfail(b, KLB_E_CUDA, std::string("batched step kernel: ") + cudaGetErrorString(e));
     b->launches += 1;
-    for (klb_t* h : b->m) {
-        handle_after_step(h);
-        const int64_t before = h->launches;
-        int r = handle_sample_if_due(h);
-        if (r != KLB_OK) return bfail(b, r, h->err);
-        b->launches += h->launches - before;
-    }
-    return KLB_OK;
+    for (klb_t* h : b->m) handle_after_step(h);
+    return batch_sample(b);
 }
 
 // capture graph_steps batched steps starting from parity p and a step count
@@ -209,6 +251,7 @@ int klb_batch_create(const klb_params* ps, int n, klb_batch_t** out) {
     b->graph_steps = b->period * (int)std::max<int64_t>(1, (64 + b->period - 1) / b->period);
     if (b->period > 512) b->use_graph = false;  // sampling periods that do not fit one graph
     if (cudaMalloc(&b->descs_dev, 2 * sizeof(InstDesc) * n) != cudaSuccess ||
+        cudaMalloc(&b->jobs_dev, 2 * sizeof(DiagJob) * n) != cudaSuccess ||
         cudaMalloc(&b->err_dev, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         return cleanup(KLB_E_NOMEM, "cudaMalloc of the batch descriptors failed");
@@ -229,6 +272,7 @@ void klb_batch_destroy(klb_batch_t* b) {
     }
     if (b->descs_dev) cudaFree(b->descs_dev);
     if (b->err_dev) cudaFree(b->err_dev);
+    if (b->jobs_dev) cudaFree(b->jobs_dev);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
 }
@@ -251,12 +295,8 @@ int klb_batch_step(klb_batch_t* b, int64_t n) {
         const bool aligned = h0->steps % b->period == 0;
         if (b->use_graph && aligned && n >= b->graph_steps) {
             // samples due before the period (the initial state) are taken eagerly
-            for (klb_t* h : b->m) {
-                const int64_t before = h->launches;
-                r = handle_sample_if_due(h);
-                if (r != KLB_OK) return bfail(b, r, h->err);
-                b->launches += h->launches - before;
-            }
+            r = batch_sample(b);
+            if (r != KLB_OK) return r;
             const int p = h0->cur;
             if (!b->graph[p]) {
                 r = build_graph(b, p);

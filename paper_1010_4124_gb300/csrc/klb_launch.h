@@ -39,6 +39,30 @@ struct InstDesc {  // aligned as its CUtensorMap member
     int tiles_x;
     int first_tile;
 };
+// The diagnostics of one member of a batch, reproduced exactly as its own
+// stand-alone reduction would do them (same tiles per CTA, same records).
+struct DiagJob {
+    const float* f;        // the member's state (buffer of the parity sampled)
+    Geom g;
+    int tiles_x, ntiles;   // its tiles for the batch's tile shape
+    int grid;              // CTAs (records) of its stand-alone reduction, f32_grid
+    int first_cta;         // its first CTA in the batched launch
+    double* partials;      // its records (grid x 8 doubles)
+    double* ring;          // its ring of samples, capacity cap
+    int cap;
+    long long* counter;    // its sample counter
+    int* err;              // its error word
+};
+// members due for a sample (bit j for member j; kMaxInstances bits)
+struct DueMask {
+    unsigned w[8];
+};
+// the records of every due member in one launch of total_ctas CTAs (variant:
+// the batch's tile shape), then their folds into their rings in one launch
+cudaError_t launch_diag_f32_batch(const StepConst<float>& c, const DiagJob* jobs, int njobs, int total_ctas,
+                                  int variant, DueMask due, cudaStream_t s);
+cudaError_t launch_diag_finalize_batch(const DiagJob* jobs, int njobs, DueMask due, cudaStream_t s);
+
 // One launch steps every grid of `descs` (ninst entries, ntiles tiles in all).
 // diag_partials (ninst == 1 only) also reduces the diagnostics of the input.
 cudaError_t launch_step_f32(const StepConst<float>& c, const InstDesc* descs, int ninst, int ntiles,

@@ -58,6 +58,16 @@ cudaError_t launch_step_f32(const StepConst<float>& c, const InstDesc* descs, in
     return launch_f32_t<16, 0>(c, descs, ninst, ntiles, diag_partials, err, spin_limit, inject, grid, stream);
 }
 
+cudaError_t launch_diag_f32_batch(const StepConst<float>& c, const DiagJob* jobs, int njobs, int total_ctas,
+                                  int variant, DueMask due, cudaStream_t s) {
+    if (njobs < 1 || total_ctas < 1) return cudaSuccess;
+    if (rows_of(variant) == 8)
+        diag_f32_batch_kernel<8><<<total_ctas, 256, 0, s>>>(c, jobs, njobs, due);
+    else
+        diag_f32_batch_kernel<16><<<total_ctas, 512, 0, s>>>(c, jobs, njobs, due);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_diag_f32(const StepConst<float>& c, const Geom& g, const float* f, double* partials, int variant,
                             cudaStream_t s) {
     int tiles_x, ntiles;

@@ -386,15 +386,17 @@ __global__ void __launch_bounds__(32 * TY, 16 / TY) step_f32_kernel(const __grid
     if (diag) diag_block_reduce<S::NT>(dv, diag_partials + 8ll * blockIdx.x);
 }
 
-// Stand-alone diagnostics of a state with the same tiles, per-CTA tile order
-// and block reduction as the fused path, so that both give the same bits.
+// Diagnostics of a state with the same tiles, per-CTA tile order and block
+// reduction as the fused path inside the step kernel, so that both give the
+// same bits: CTA `cta` of `ncta` takes tiles cta, cta + ncta, ... and writes
+// one partial record.
 template <int TY>
-__global__ void __launch_bounds__(32 * TY) diag_f32_kernel(const StepConst<float> c, const Geom g, int tiles_x,
-                                                           int ntiles, const float* __restrict__ f,
-                                                           double* __restrict__ partials) {
+__device__ __forceinline__ void diag_cta(const StepConst<float>& c, const Geom& g, int tiles_x, int ntiles,
+                                         const float* __restrict__ f, double* __restrict__ partial, int cta,
+                                         int ncta) {
     const int tid = threadIdx.x, ty = tid >> 5, lane = tid & 31;
     double dv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    for (int t = cta; t < ntiles; t += ncta) {
         const TileInfo ti = tile_info<TY>(t, tiles_x);
         const int ix = ti.x0 + lane, iy = ti.y0 + ty;
         const bool active = ix >= 0 && ix < g.nx && iy < g.ny;
@@ -408,7 +410,32 @@ __global__ void __launch_bounds__(32 * TY) diag_f32_kernel(const StepConst<float
 #pragma unroll
         for (int j = 0; j < 8; ++j) dv[j] = (j == 4 || j == 5 || j == 7) ? fmax(dv[j], v[j]) : dv[j] + v[j];
     }
-    diag_block_reduce<32 * TY>(dv, partials + 8ll * blockIdx.x);
+    diag_block_reduce<32 * TY>(dv, partial);
+}
+
+template <int TY>
+__global__ void __launch_bounds__(32 * TY) diag_f32_kernel(const StepConst<float> c, const Geom g, int tiles_x,
+                                                           int ntiles, const float* __restrict__ f,
+                                                           double* __restrict__ partials) {
+    diag_cta<TY>(c, g, tiles_x, ntiles, f, partials + 8ll * blockIdx.x, blockIdx.x, gridDim.x);
+}
+
+// The stand-alone reductions of several members in one launch: CTA b belongs
+// to the job whose CTA range holds b, and does that job's CTA b - first_cta.
+template <int TY>
+__global__ void __launch_bounds__(32 * TY) diag_f32_batch_kernel(const StepConst<float> c,
+                                                                 const DiagJob* __restrict__ jobs, int njobs,
+                                                                 DueMask due) {
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].first_cta <= (int)blockIdx.x) lo = mid;
+        else hi = mid - 1;
+    }
+    if (!((due.w[lo >> 5] >> (lo & 31)) & 1u)) return;  // uniform across the CTA
+    const DiagJob& J = jobs[lo];
+    const int v = (int)blockIdx.x - J.first_cta;
+    diag_cta<TY>(c, J.g, J.tiles_x, J.ntiles, J.f, J.partials + 8ll * v, v, J.grid);
 }
 
 // dynamic shared memory of the kernel instance, set once per process
