@@ -603,7 +603,7 @@ def main():
     ap.add_argument("--workload", default="khi4096", choices=["khi4096", "khi2048", "khi512"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--variant", type=int, default=-1,
-                    help="FP32 kernel tile shape (0: 31x16, 1: 31x8); -1 picks the faster by timing both")
+                    help="FP32 kernel tile shape (0: 32x16, 1: 32x8); -1 picks the faster by timing both")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--sweep-steps", type=int, default=280)
