@@ -144,7 +144,8 @@ int klb_mean_density(klb_t* h, double* out, int on_device);
  *   [0] sum rho, [1] sum rho u_x, [2] sum rho u_y, [3] sum rho (T + |u|^2/2),
  *   [4] max |u_y|, [5] max rho u_y^2 / 2, [6] sum rho u_y^2 / 2,
  * sums over interior nodes (unweighted), accumulated in FP64 in a fixed order
- * (deterministic).  Copies min(cap, available) records, oldest first, into
+ * (deterministic); an FP32 grid forms each node's values in FP32 and sums
+ * them per thread as compensated FP32 pairs before the FP64 reduction.  Copies min(cap, available) records, oldest first, into
  * out[cap][7] (host) and the number copied into *count.  Synchronises; returns
  * KLB_E_NONFINITE if any sampled state had rho or T non-finite or <= 0. */
 int klb_diagnostics(klb_t* h, double* out, int64_t cap, int64_t* count);

@@ -50,9 +50,9 @@ __global__ void __launch_bounds__(256) diag_finalize_kernel(const double* __rest
 }
 
 // the folds of the due members of a batch, one block each
-__global__ void __launch_bounds__(256) diag_finalize_batch_kernel(const DiagJob* __restrict__ jobs, DueMask due) {
+__global__ void __launch_bounds__(256) diag_finalize_batch_kernel(const DiagJob* __restrict__ jobs, const DueMask due) {
     const int j = blockIdx.x;
-    if (!((due.w[j >> 5] >> (j & 31)) & 1u)) return;  // uniform across the block
+    if (!KLB_DUE_BIT(due, j)) return;  // uniform across the block
     const DiagJob& J = jobs[j];
     fold_records(J.partials, J.grid, J.ring, J.cap, J.counter, J.err);
 }

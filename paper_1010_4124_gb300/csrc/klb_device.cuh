@@ -457,6 +457,80 @@ __device__ __forceinline__ void node_diag(const NodeEq<T>& s, bool active, doubl
     }
 }
 
+// The same diagnostics of an FP32 state, accumulated per thread without FP64
+// work per node (FP64 runs at a small fraction of the FP32 rate on this GPU):
+// the values of a node in FP32 (explicitly rounded, like the state they come
+// from), each sum carried as an unevaluated pair hi + lo updated by Knuth's
+// TwoSum (the rounding error of every addition is kept in lo, so the pair
+// tracks the exact sum of the FP32 values to about n eps^2 relative after n
+// additions), the maxima in FP32 and the flag as an integer.  A warp merges
+// its threads' pairs the same way; its record (hi + lo in FP64, the layout of
+// node_diag's) enters the FP64 combination across warps.
+struct DiagAccF32 {
+    float hi[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, lo[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    float m4 = 0.f, m5 = 0.f;
+    int bad = 0;
+    // hi + lo <- hi + lo + x with the rounding error of hi + x carried in lo
+    __device__ __forceinline__ void two_sum(int k, float x) {
+        const float s = __fadd_rn(hi[k], x);
+        const float xb = __fsub_rn(s, hi[k]);
+        const float ha = __fsub_rn(s, xb);
+        const float e = __fadd_rn(__fsub_rn(hi[k], ha), __fsub_rn(x, xb));
+        hi[k] = s;
+        lo[k] = __fadd_rn(lo[k], e);
+    }
+    __device__ __forceinline__ void add(const NodeEq<float>& s, bool active) {
+        if (!active) return;
+        const float r = s.rho, u = s.ux, w = s.uy, Tm = s.Tm;
+        const float e = __fmul_rn(r, fmaf(0.5f, fmaf(u, u, __fmul_rn(w, w)), Tm));
+        const float k = __fmul_rn(__fmul_rn(__fmul_rn(0.5f, r), w), w);
+        two_sum(0, r);
+        two_sum(1, __fmul_rn(r, u));
+        two_sum(2, __fmul_rn(r, w));
+        two_sum(3, e);
+        two_sum(4, k);
+        m4 = fmaxf(m4, fabsf(w));
+        m5 = fmaxf(m5, k);
+        bad |= (r > 0.f && Tm > 0.f) ? 0 : 1;  // also catches NaN
+    }
+    // hi + lo <- hi + lo + (h2 + l2): TwoSum of the leading parts, the
+    // trailing parts and the rounding error added into lo
+    __device__ __forceinline__ void merge(int k, float h2, float l2) {
+        const float s = __fadd_rn(hi[k], h2);
+        const float xb = __fsub_rn(s, hi[k]);
+        const float ha = __fsub_rn(s, xb);
+        const float e = __fadd_rn(__fsub_rn(hi[k], ha), __fsub_rn(h2, xb));
+        hi[k] = s;
+        lo[k] = __fadd_rn(__fadd_rn(lo[k], l2), e);
+    }
+    // the warp's accumulators combined into lane 0 (a fixed shuffle tree, so
+    // deterministic), in FP32 pairs and FP32 maxima
+    __device__ __forceinline__ void warp_reduce() {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                const float h2 = __shfl_down_sync(0xffffffffu, hi[k], o);
+                const float l2 = __shfl_down_sync(0xffffffffu, lo[k], o);
+                merge(k, h2, l2);
+            }
+            m4 = fmaxf(m4, __shfl_down_sync(0xffffffffu, m4, o));
+            m5 = fmaxf(m5, __shfl_down_sync(0xffffffffu, m5, o));
+            bad |= __shfl_down_sync(0xffffffffu, bad, o);
+        }
+    }
+    __device__ __forceinline__ void record(double v[8]) const {
+        v[0] = __dadd_rn((double)hi[0], (double)lo[0]);
+        v[1] = __dadd_rn((double)hi[1], (double)lo[1]);
+        v[2] = __dadd_rn((double)hi[2], (double)lo[2]);
+        v[3] = __dadd_rn((double)hi[3], (double)lo[3]);
+        v[4] = m4;
+        v[5] = m5;
+        v[6] = __dadd_rn((double)hi[4], (double)lo[4]);
+        v[7] = bad ? 1.0 : 0.0;
+    }
+};
+
 // Block reduction of the diagnostics (FP64) to one partial record: sums for
 // slots 0-3 and 6, maxima for 4, 5 and the flag 7.  The shuffle tree and the
 // warp order are fixed, so the result is deterministic.
@@ -473,6 +547,27 @@ __device__ __forceinline__ void diag_block_reduce(double v[8], double* __restric
             x = (k == 4 || k == 5 || k == 7) ? fmax(x, y) : x + y;
         }
         if (lane == 0) red[w][k] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        const int k = threadIdx.x;
+        double x = red[0][k];
+        for (int i = 1; i < NT / 32; ++i) x = (k == 4 || k == 5 || k == 7) ? fmax(x, red[i][k]) : x + red[i][k];
+        partial[k] = x;
+    }
+}
+// The same record from FP32 accumulators: the warp tree in FP32 pairs, the
+// per-warp records across warps in FP64 in the order of node_diag's.
+template <int NT>
+__device__ __forceinline__ void diag_block_reduce(DiagAccF32 a, double* __restrict__ partial) {
+    __shared__ double red[NT / 32][8];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    a.warp_reduce();
+    if (lane == 0) {
+        double v[8];
+        a.record(v);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) red[w][k] = v[k];
     }
     __syncthreads();
     if (threadIdx.x < 8) {

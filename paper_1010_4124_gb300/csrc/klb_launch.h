@@ -57,6 +57,12 @@ struct DiagJob {
 struct DueMask {
     unsigned w[8];
 };
+// bit j of the mask, selected with constant indices only (a dynamically
+// indexed parameter would be copied to local memory)
+#define KLB_DUE_BIT(m, j)                                                                             \
+    ((((j) >> 5) == 0 ? (m).w[0] : ((j) >> 5) == 1 ? (m).w[1] : ((j) >> 5) == 2 ? (m).w[2]            \
+      : ((j) >> 5) == 3 ? (m).w[3] : ((j) >> 5) == 4 ? (m).w[4] : ((j) >> 5) == 5 ? (m).w[5]          \
+      : ((j) >> 5) == 6 ? (m).w[6] : (m).w[7]) >> ((j) & 31) & 1u)
 // the records of every due member in one launch of total_ctas CTAs (variant:
 // the batch's tile shape), then their folds into their rings in one launch
 cudaError_t launch_diag_f32_batch(const StepConst<float>& c, const DiagJob* jobs, int njobs, int total_ctas,

@@ -27,8 +27,9 @@
 //  * Per node: moments, F_k, f^(0) and the conservative BGK relaxation
 //    (ArithF32::collide) in registers, the flux divergence, and a coalesced
 //    store; nodes next to a periodic or outflow side also write their ghost
-//    images.  Optionally the diagnostics of the input nodes are reduced (FP64)
-//    per CTA; the stand-alone kernel below reproduces the same order.
+//    images.  Optionally the diagnostics of the input nodes are reduced per
+//    CTA (FP32 node values, FP64 sums); the stand-alone kernel below
+//    reproduces the same order.
 #pragma once
 #include "klb_device.cuh"
 #include "klb_launch.h"
@@ -282,7 +283,7 @@ __global__ void __launch_bounds__(32 * TY, 16 / TY) step_f32_kernel(const __grid
     }
     __syncthreads();
 
-    double dv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    DiagAccF32 acc;
     const bool diag = diag_partials != nullptr;
     // fields of the instance of the current tile, read from global memory
     // only when the instance changes (tiles of one instance are contiguous)
@@ -325,12 +326,7 @@ __global__ void __launch_bounds__(32 * TY, 16 / TY) step_f32_kernel(const __grid
 #pragma unroll
         for (int q = 0; q < NQ; ++q) f[q] = tile[q * S::PLANE + r * v3::SXB + s];
         const NodeEq<float> st = ArithF32::node_state(c, f);
-        if (diag) {
-            double v[8];
-            node_diag(st, active, v);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) dv[j] = (j == 4 || j == 5 || j == 7) ? fmax(dv[j], v[j]) : dv[j] + v[j];
-        }
+        if (diag) acc.add(st, active);
         ArithF32::collide(c, st, f);  // f <- post-collision values
         edge_faces<TY, SCH>(c, tile, r, lane, edge);
         // x and y faces of the 12 velocities with two components, packed in pairs
@@ -383,7 +379,7 @@ __global__ void __launch_bounds__(32 * TY, 16 / TY) step_f32_kernel(const __grid
         // the next tile's middle barrier.  With one, wait for all readers.
         if (S::YB == 1) __syncthreads();
     }
-    if (diag) diag_block_reduce<S::NT>(dv, diag_partials + 8ll * blockIdx.x);
+    if (diag) diag_block_reduce<S::NT>(acc, diag_partials + 8ll * blockIdx.x);
 }
 
 // Diagnostics of a state with the same tiles, per-CTA tile order and block
@@ -395,22 +391,29 @@ __device__ __forceinline__ void diag_cta(const StepConst<float>& c, const Geom& 
                                          const float* __restrict__ f, double* __restrict__ partial, int cta,
                                          int ncta) {
     const int tid = threadIdx.x, ty = tid >> 5, lane = tid & 31;
-    double dv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int t = cta; t < ntiles; t += ncta) {
+    // the node of tile t for this thread, its activity and its 19 values
+    auto load = [&](int t, float fl[NQ]) {
         const TileInfo ti = tile_info<TY>(t, tiles_x);
         const int ix = ti.x0 + lane, iy = ti.y0 + ty;
         const bool active = ix >= 0 && ix < g.nx && iy < g.ny;
-        float fl[NQ];
 #pragma unroll
         for (int q = 0; q < NQ; ++q)
             fl[q] = active ? f[q * g.plane + (long long)(iy + GY) * g.px + (ix + GX)] : 1.f;
-        const NodeEq<float> st = ArithF32::node_state(c, fl);
-        double v[8];
-        node_diag(st, active, v);
+        return active;
+    };
+    DiagAccF32 acc;
+    // the loads of the next tile are issued before the current one is reduced
+    // (two tiles in flight per thread); the accumulation order is unchanged
+    float cur[NQ], nxt[NQ];
+    bool act = cta < ntiles ? load(cta, cur) : false;
+    for (int t = cta; t < ntiles; t += ncta) {
+        const bool act_n = t + ncta < ntiles ? load(t + ncta, nxt) : false;
+        acc.add(ArithF32::node_state(c, cur), act);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) dv[j] = (j == 4 || j == 5 || j == 7) ? fmax(dv[j], v[j]) : dv[j] + v[j];
+        for (int q = 0; q < NQ; ++q) cur[q] = nxt[q];
+        act = act_n;
     }
-    diag_block_reduce<32 * TY>(dv, partial);
+    diag_block_reduce<32 * TY>(acc, partial);
 }
 
 template <int TY>
@@ -425,14 +428,14 @@ __global__ void __launch_bounds__(32 * TY) diag_f32_kernel(const StepConst<float
 template <int TY>
 __global__ void __launch_bounds__(32 * TY) diag_f32_batch_kernel(const StepConst<float> c,
                                                                  const DiagJob* __restrict__ jobs, int njobs,
-                                                                 DueMask due) {
+                                                                 const DueMask due) {
     int lo = 0, hi = njobs - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if (jobs[mid].first_cta <= (int)blockIdx.x) lo = mid;
         else hi = mid - 1;
     }
-    if (!((due.w[lo >> 5] >> (lo & 31)) & 1u)) return;  // uniform across the CTA
+    if (!KLB_DUE_BIT(due, lo)) return;  // uniform across the CTA
     const DiagJob& J = jobs[lo];
     const int v = (int)blockIdx.x - J.first_cta;
     diag_cta<TY>(c, J.g, J.tiles_x, J.ntiles, J.f, J.partials + 8ll * v, v, J.grid);
