@@ -48,6 +48,29 @@ def test_members_match_grids_stepped_alone(variant, graph):
         assert np.array_equal(da, db)
 
 
+def test_many_members_with_mixed_sampling_match_grids_stepped_alone():
+    # more than 32 members (the due-for-a-sample mask spans two words), three
+    # sampling cadences (partial masks) and uneven sizes: every member's state
+    # and diagnostics series equal those of the grid stepped alone.  The
+    # common period is 12 steps and one graph holds 72: 96 steps replay one
+    # graph and take 24 steps one by one.
+    rng = np.random.default_rng(11)
+    steps = 96
+    pbs = [inputs.khi(int(rng.integers(33, 90)), int(rng.integers(20, 70)), steps, Dv=float(rng.integers(2, 9)),
+                      Drho=float(rng.integers(2, 13)), sample_every=(3, 4, 6)[i % 3]) for i in range(37)]
+    with klb.KlbBatch.from_problems(pbs) as b:
+        for m, pb in zip(b.members, pbs):
+            m.init_fields(*inputs.fields(pb))
+        b.step(steps)
+        b.sync()
+        got = [(m.get_f(), m.diagnostics()) for m in b.members]
+    for (fb, db), pb in zip(got, pbs):
+        fa, da = _alone(pb, steps, 0)
+        assert np.array_equal(fa, fb)
+        assert da.shape == (steps // pb.sample_every + 1, 7)
+        assert np.array_equal(da, db)
+
+
 def test_autotune_leaves_the_run_unchanged():
     pbs = _problems()
     with klb.KlbBatch.from_problems(pbs) as b:
