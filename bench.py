@@ -606,7 +606,7 @@ def main():
                     help="FP32 kernel tile shape (0: 32x16, 1: 32x8); -1 picks the faster by timing both")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
-    ap.add_argument("--sweep-steps", type=int, default=280)
+    ap.add_argument("--sweep-steps", type=int, default=2000)
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-schemes", action="store_true")
     ap.add_argument("--no-physics", action="store_true")
