@@ -504,7 +504,6 @@ static int flush_sample(klb_t* h) {
     h->pending_sample = false;
     return KLB_OK;
 }
-int fdlb::handle_sample_if_due(klb_t* h) { return flush_sample(h); }
 
 static int read_nsamples(klb_t* h, long long* n) {
     CK(h, cudaMemcpyAsync(n, h->nsamp_dev, sizeof(long long), cudaMemcpyDeviceToHost, h->stream));

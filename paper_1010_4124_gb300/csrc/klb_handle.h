@@ -62,5 +62,4 @@ void step_constants(const klb_params& p, StepConst<double>& c);
 int handle_fail(klb_t* h, int code, const std::string& msg);
 int handle_upload_descs(klb_t* h);  // (re)build the FP32 descriptors and the tile count
 void handle_after_step(klb_t* h);   // advance the step counter and the parity
-int handle_sample_if_due(klb_t* h); // enqueue the diagnostics of the current state if a sample is due
 }  // namespace fdlb
