@@ -87,14 +87,14 @@ static int vjp_step(klb_adj_t* a, const void* f, const void* lam_in, void* lam_o
     // one thread per (face, velocity) and per (node, velocity)
     const long long n = (long long)g.nx * g.ny;
     const long long nfmax = std::max((long long)(g.nx + 1) * g.ny, (long long)g.nx * (g.ny + 1));
-    adj_faces_kernel<T><<<dim3(grid_of(nfmax), (NQ - 1) + 12), 256, 0, h->stream>>>(
-        c, g, (const T*)f, (const T*)lam_in, (T*)a->Dx, (T*)a->Dy);
-    adj_node_kernel<T><<<grid_of(n), 256, 0, h->stream>>>(c, g, (const T*)f, (const T*)lam_in, (T*)a->Nb);
+    // face gradients and node sensitivities (independent), then the gather
+    adj_faces_kernel<T><<<dim3(grid_of(std::max(nfmax, n)), (NQ - 1) + 12 + 1), 256, 0, h->stream>>>(
+        c, g, (const T*)f, (const T*)lam_in, (T*)a->Dx, (T*)a->Dy, (T*)a->Nb);
     adj_gather_kernel<T><<<dim3(grid_of(n), NQ), 256, 0, h->stream>>>(
         c, g, (const T*)lam_in, (const T*)a->Nb, (const T*)a->Dx, (const T*)a->Dy, T(coef), (T*)lam_out);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return afail(a, KLB_E_CUDA, std::string("adjoint kernels: ") + cudaGetErrorString(e));
-    h->launches += 3;
+    h->launches += 2;
     return KLB_OK;
 }
 

@@ -236,20 +236,11 @@ __device__ __forceinline__ void adj_faces_y(const StepConst<T>& c, const Geom& g
     }
 }
 
-// all face gradients in one launch: blockIdx.y < 18 the x faces of velocity
-// blockIdx.y + 1, else the y faces of y slot blockIdx.y - 18
-template <typename T>
-__global__ void adj_faces_kernel(const StepConst<T> c, const Geom g, const T* __restrict__ f,
-                                 const T* __restrict__ lam, T* __restrict__ Dx, T* __restrict__ Dy) {
-    if (blockIdx.y < NQ - 1) adj_faces_x(c, g, f, lam, Dx, (int)blockIdx.y);
-    else adj_faces_y(c, g, f, lam, Dy, (int)blockIdx.y - (NQ - 1));
-}
-
 // Per node: the sensitivity of f^(0) carried to the moments (four values,
 // feq_vjp_moments) and u_y (for the source term), into N[5][nx * ny].
 template <typename T>
-__global__ void adj_node_kernel(const StepConst<T> c, const Geom g, const T* __restrict__ f,
-                                const T* __restrict__ lam, T* __restrict__ N) {
+__device__ __forceinline__ void adj_node(const StepConst<T>& c, const Geom& g, const T* __restrict__ f,
+                                         const T* __restrict__ lam, T* __restrict__ N) {
     const long long n = (long long)g.nx * g.ny;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(t % g.nx), j = (int)(t / g.nx);
@@ -267,6 +258,18 @@ __global__ void adj_node_kernel(const StepConst<T> c, const Geom g, const T* __r
         for (int k = 0; k < 4; ++k) N[k * n + t] = gm[k];
         N[4 * n + t] = m.uy;
     }
+}
+
+// Everything of a reverse step that reads only f^n and lambda^{n+1}, in one
+// launch: blockIdx.y < 18 the x faces of velocity blockIdx.y + 1, 18 .. 29 the
+// y faces of y slot blockIdx.y - 18, 30 the per-node moment sensitivities.
+template <typename T>
+__global__ void adj_faces_kernel(const StepConst<T> c, const Geom g, const T* __restrict__ f,
+                                 const T* __restrict__ lam, T* __restrict__ Dx, T* __restrict__ Dy,
+                                 T* __restrict__ N) {
+    if (blockIdx.y < NQ - 1) adj_faces_x(c, g, f, lam, Dx, (int)blockIdx.y);
+    else if (blockIdx.y < NQ - 1 + 12) adj_faces_y(c, g, f, lam, Dy, (int)blockIdx.y - (NQ - 1));
+    else adj_node(c, g, f, lam, N);
 }
 
 // stencil positions that hold node i's value: the node itself and, next to a
