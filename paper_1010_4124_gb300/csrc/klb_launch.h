@@ -22,7 +22,7 @@ cudaError_t launch_step(const CUtensorMap& in_map, const StepConst<T>& c, const 
                         double* diag_partials, int* err, long long spin_limit, int inject, cudaStream_t stream);
 // FP64 step: TX x TY tiles, one thread per node (klb_step_f64.cu)
 void f64_tile(int* tx, int* ty);
-// FP32 step (klb_step_f32.cu): persistent CTAs over tiles of 31 columns x
+// FP32 step (klb_step_f32.cu): persistent CTAs over tiles of 32 columns x
 // 16 rows (variant 0) or 8 rows (variant 1); f32_grid = number of CTAs (and
 // of diagnostics partial records); f32_box = the TMA box of one tile.
 void f32_tiles(int nx, int ny, int variant, int* tiles_x, int* ntiles);
