@@ -131,6 +131,34 @@ def test_diagnostics_series_parity(prec, tol):
         assert np.abs(d[:, k] - dref[:, k]).max() <= tol * scale, k
 
 
+@pytest.mark.parametrize("variant", [0, 1])
+def test_fp32_diagnostics_equal_the_oracle_sums_of_the_same_state(variant):
+    # The FP32 diagnostics (FP32 node values, compensated FP32 partial sums,
+    # FP64 across warps and CTAs) against the oracle's FP64 diagnostics of the
+    # very same FP32 state (read back exactly): every interior node counted
+    # once on ragged tiles (one node missed would be 1.7e-6 of the mass), the
+    # sums accurate to the rounding of the node values.  Sample 0 is reduced
+    # inside the first step's kernel, sample 1 by the stand-alone kernel.
+    pb = inputs.khi(1000, 600, 10, Dv=4.0, Drho=4.0, sample_every=10)
+    p = oracle_params(pb)
+    with gpu_handle(pb, "fp32") as h:
+        h.variant = variant
+        h.init_fields(*inputs.fields(pb))
+        f0 = h.get_f()
+        h.step(10)
+        f1 = h.get_f()
+        d = h.diagnostics()
+    assert d.shape == (2, 7)
+    for got, f in ((d[0], f0), (d[1], f1)):
+        ref = core.diag(p, f)
+        mass = abs(ref[0])
+        assert abs(got[0] - ref[0]) <= 1e-8 * mass, (got[0], ref[0])
+        assert abs(got[1] - ref[1]) <= 1e-6 * mass and abs(got[2] - ref[2]) <= 1e-6 * mass
+        assert abs(got[3] - ref[3]) <= 1e-6 * abs(ref[3])
+        for k in (4, 5, 6):
+            assert abs(got[k] - ref[k]) <= 1e-5 * abs(ref[k]), (k, got[k], ref[k])
+
+
 def test_conservation_fp64_periodic():
     pb = _problem(80, 72, "periodic", "periodic")
     fields = inputs.smooth_random_fields(80, 72, seed=2, amp=0.1)
