@@ -225,6 +225,68 @@ def test_roofline_4096_windows_parity():
         assert max(errs["rho"], errs["u"], errs["T"]) <= 1e-5, ((y0, x0), errs)
 
 
+class _DeviceState:
+    """The current FP32 state of a handle as a device array [19][rows][pitch]
+    (rows = ghost rows included), for torch to view without a copy."""
+
+    def __init__(self, h):
+        base, pitch, plane, self.gx, self.gy = h.layout()
+        self.__cuda_array_interface__ = {"shape": (19, plane // pitch, pitch), "typestr": "<f4",
+                                         "data": (base, False), "version": 3, "strides": None}
+
+
+def test_fp32_step_beyond_2g_elements_windows_parity():
+    # 16384 x 16384 FP32: 5.1 G elements per buffer (offsets past 2^31), 41 GB
+    # of state.  The KHI fields are built on the device; windows of the state
+    # (with a 3-node rim) are read through the library's layout before and
+    # after one more step, and one oracle step on each window equals the GPU's
+    # step on the window's core (rows beyond the domain: the outflow copy).
+    torch = pytest.importorskip("torch")
+    n, W = 16384, 40
+    pb = inputs.khi(n, n, 3, Dv=16.0, Drho=16.0)
+    dev = torch.device("cuda")
+    y = ((torch.arange(n, device=dev, dtype=torch.float64) - n / 2 + 0.5) * pb.dy)[:, None]
+    x = (torch.arange(n, device=dev, dtype=torch.float64) * pb.dx)[None, :]
+    th = torch.tanh(y / (16.0 * pb.dy))
+    rho = (3.0 + 2.0 * th).expand(n, n).contiguous()
+    ux = (0.25 * th).expand(n, n).contiguous()
+    T = (1.5 / rho).contiguous()
+    uy = (0.01 * torch.sin(2 * np.pi * x / (n * pb.dx)) * torch.exp(-(y / (0.05 * n * pb.dy)) ** 2)).contiguous()
+    del th
+    rng = np.random.default_rng(16384)
+    corners = [(0, 0), (n - W, n - W), (n // 2 - W // 2, n // 2 - W // 2), (0, n - W)] + \
+        [tuple(int(v) for v in rng.integers(0, n - W, 2)) for _ in range(3)]
+
+    def windows(h, rim):
+        st = torch.as_tensor(_DeviceState(h), device=dev)
+        out = []
+        for (y0, x0) in corners:
+            ys = torch.as_tensor(np.clip(np.arange(y0 - rim, y0 + W + rim), 0, n - 1) + 3, device=dev)
+            xs = torch.as_tensor(np.arange(x0 - rim, x0 + W + rim) % n + 4, device=dev)
+            out.append(st.index_select(1, ys).index_select(2, xs).double().cpu().numpy())
+        return out
+
+    with gpu_handle(pb, "fp32") as h:
+        h.init_fields(rho, ux, uy, T)
+        h.sync()  # the fields are read on the handle's stream
+        del rho, ux, uy, T
+        h.step(2)
+        h.sync()
+        _, _, _, gx, gy = h.layout()
+        assert (gx, gy) == (4, 3)
+        fa = windows(h, 3)
+        h.step(1)
+        h.sync()
+        fb = windows(h, 0)
+    for (y0, x0), wa, got in zip(corners, fa, fb):
+        pw = core.Params(nx=W + 6, ny=W + 6, dx=pb.dx, dy=pb.dy, dt=pb.dt, tau=pb.tau,
+                         bc_x=("periodic", "periodic"), bc_y=("periodic", "periodic"))
+        ref = core.step(pw, wa)[:, 3:-3, 3:-3]
+        assert rel_err_global(got, ref) <= 1e-5, (y0, x0)
+        errs = rel_err_fields(got, ref, core.Params(nx=W, ny=W, dx=pb.dx, dy=pb.dy, dt=pb.dt, tau=pb.tau))
+        assert max(errs["rho"], errs["u"], errs["T"]) <= 1e-5, ((y0, x0), errs)
+
+
 def test_step_before_init_and_bad_args():
     pb = _problem(16, 16, "periodic", "periodic")
     with gpu_handle(pb, "fp32") as h:
