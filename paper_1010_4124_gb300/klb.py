@@ -117,17 +117,23 @@ def _check(h, code):
         raise KlbError(code, msg.decode() if msg else "")
 
 
-def _ptr(a):
-    """(pointer, on_device) of a numpy array or a torch tensor (float64, contiguous)."""
+def _ptr(a, n=None):
+    """(pointer, on_device) of a numpy array or a torch tensor (float64,
+    contiguous, and of n elements when n is given: the library reads or writes
+    exactly that many through the pointer, so a shorter array is refused here)."""
     if a is None:
         return None, 0
     if isinstance(a, np.ndarray):
         if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
             raise TypeError("numpy arrays must be C-contiguous float64")
+        if n is not None and a.size != n:
+            raise ValueError(f"array of {a.size} elements where {n} are needed")
         return a.ctypes.data, 0
     # torch tensor
     if str(a.dtype) != "torch.float64" or not a.is_contiguous():
         raise TypeError("tensors must be contiguous float64")
+    if n is not None and a.numel() != n:
+        raise ValueError(f"tensor of {a.numel()} elements where {n} are needed")
     return a.data_ptr(), 1 if a.is_cuda else 0
 
 
@@ -192,20 +198,20 @@ class Klb:
 
     # --- entry points ------------------------------------------------------
     def init_fields(self, rho, ux, uy, T):
-        ptrs = [_ptr(a) for a in (rho, ux, uy, T)]
+        ptrs = [_ptr(a, self.nx * self.ny) for a in (rho, ux, uy, T)]
         ond = {p[1] for p in ptrs}
         if len(ond) != 1:
             raise TypeError("all four fields must live on the same side (host or device)")
         _check(self.h, lib().klb_init_fields(self.h, *[p[0] for p in ptrs], ond.pop()))
 
     def set_f(self, f):
-        p, d = _ptr(f)
+        p, d = _ptr(f, 19 * self.nx * self.ny)
         _check(self.h, lib().klb_set_f(self.h, p, d))
 
     def get_f(self, out=None):
         if out is None:
             out = np.empty((19, self.ny, self.nx))
-        p, d = _ptr(out)
+        p, d = _ptr(out, 19 * self.nx * self.ny)
         _check(self.h, lib().klb_get_f(self.h, p, d))
         return out
 
@@ -218,7 +224,7 @@ class Klb:
     def moments(self, out=None):
         if out is None:
             out = tuple(np.empty((self.ny, self.nx)) for _ in range(4))
-        ptrs = [_ptr(a) for a in out]
+        ptrs = [_ptr(a, self.nx * self.ny) for a in out]
         ond = {p[1] for p in ptrs if p[0] is not None}
         _check(self.h, lib().klb_moments(self.h, *[p[0] for p in ptrs], ond.pop() if ond else 0))
         return out
@@ -227,7 +233,7 @@ class Klb:
         """The averaged density profile rho_bar[ny] (mean of rho along x)."""
         if out is None:
             out = np.empty(self.ny)
-        pa, dev = _ptr(out)
+        pa, dev = _ptr(out, self.ny)
         _check(self.h, lib().klb_mean_density(self.h, pa, dev))
         return out
 
@@ -395,7 +401,7 @@ class KlbAdjoint:
         self.close()
 
     def forward(self, rho, ux, uy, T):
-        ptrs = [_ptr(x) for x in (rho, ux, uy, T)]
+        ptrs = [_ptr(x, self.nx * self.ny) for x in (rho, ux, uy, T)]
         ond = {p[1] for p in ptrs}
         if len(ond) != 1:
             raise TypeError("all four fields must live on the same side (host or device)")
@@ -407,7 +413,7 @@ class KlbAdjoint:
     def backward(self, g_ke: float, g_gamma: float, out=None):
         if out is None:
             out = tuple(np.empty((self.ny, self.nx)) for _ in range(4))
-        ptrs = [_ptr(x) for x in out]
+        ptrs = [_ptr(x, self.nx * self.ny) for x in out]
         ond = {p[1] for p in ptrs}
         _acheck(self.a, lib().klb_adjoint_backward(self.a, float(g_ke), float(g_gamma), *[p[0] for p in ptrs],
                                                    ond.pop()))
@@ -416,8 +422,8 @@ class KlbAdjoint:
     def vjp(self, lam_N, out=None):
         if out is None:
             out = np.empty((19, self.ny, self.nx))
-        pa, da = _ptr(lam_N)
-        pb, db = _ptr(out)
+        pa, da = _ptr(lam_N, 19 * self.nx * self.ny)
+        pb, db = _ptr(out, 19 * self.nx * self.ny)
         if da != db:
             raise TypeError("lam_N and the output must live on the same side")
         _acheck(self.a, lib().klb_adjoint_vjp(self.a, pa, pb, da))

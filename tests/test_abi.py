@@ -4,6 +4,7 @@ import ctypes as C
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -88,3 +89,25 @@ def test_scheme_validation_without_gpu(lib):
     with pytest.raises(klb.KlbError) as e:
         klb.KlbAdjoint(q, 4, 2)
     assert e.value.code == -1
+
+
+def test_binding_refuses_arrays_of_the_wrong_size():
+    # the library reads or writes exactly n elements through each pointer; the
+    # binding checks the count before any call (a shorter array would be read
+    # past its end)
+    from paper_1010_4124_gb300 import klb
+    a = np.zeros((4, 5))
+    assert klb._ptr(a, 20) == (a.ctypes.data, 0)
+    with pytest.raises(ValueError):
+        klb._ptr(a, 21)
+    with pytest.raises(ValueError):
+        klb._ptr(np.zeros(19 * 20 - 1), 19 * 20)
+    with pytest.raises(TypeError):
+        klb._ptr(np.zeros(20, dtype=np.float32), 20)
+    with pytest.raises(TypeError):
+        klb._ptr(np.zeros((5, 4)).T, 20)  # not C-contiguous
+    torch = pytest.importorskip("torch")
+    t = torch.zeros(20, dtype=torch.float64)
+    assert klb._ptr(t, 20) == (t.data_ptr(), 0)
+    with pytest.raises(ValueError):
+        klb._ptr(t, 19)
