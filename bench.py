@@ -338,8 +338,8 @@ def sweep_measure(steps: int, torch):
     """The batched D_v x D_rho sweep (32 KHI instances on uneven grids drawn by
     seed, FP32, diagnostics every 10 steps): one persistent launch per step
     over all instances, replayed from a CUDA graph, tiles picked by the
-    autotuner -- against looping the plain single-grid step over the 32
-    instances one after another on the same GPU."""
+    autotuner -- against looping the plain single-grid step (same tile shape)
+    over the 32 instances one after another on the same GPU."""
     import numpy as np
     from paper_1010_4124_gb300 import inputs, klb
     pbs = inputs.sweep_instances(steps)
@@ -362,10 +362,11 @@ def sweep_measure(steps: int, torch):
         t_batch = e0.elapsed_time(e1) * 1e-3
         launches = bt.launch_count - n0
         tiles = bt.tiles
-    # the plain step, looped over the instances
+    # the plain step, looped over the instances, with the batch's tile shape
     hs = []
     for pb, fl in zip(pbs, fields):
         h = klb.Klb.from_problem(pb, precision="fp32", stream=stream.cuda_stream)
+        h.variant = variant
         h.init_fields(*fl)
         h.step(3)
         hs.append(h)
