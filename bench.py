@@ -526,8 +526,10 @@ def schemes_measure(workload: str, steps: int, torch):
 
 
 def _band(pb, rows: int):
-    """A full-width band of `rows` rows centred on the shear layer of the workload."""
+    """A full-width band of `rows` rows (at most the workload's) centred on the
+    shear layer of the workload."""
     from paper_1010_4124_gb300 import inputs
+    rows = min(rows, pb.ny)
     band = pb.with_(ny=rows)
     full = inputs.fields(pb)
     j0 = pb.ny // 2 - rows // 2

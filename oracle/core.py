@@ -104,6 +104,15 @@ def _ptr(a: np.ndarray):
     return a.ctypes.data_as(C.c_void_p)
 
 
+def _shaped(x, shape, cs: bool):
+    """x as a contiguous array of exactly `shape` (the C code reads that many
+    elements; a mismatch is refused here rather than read past)."""
+    a = _arr(x, cs)
+    if a.shape != tuple(shape):
+        raise ValueError(f"array of shape {a.shape} where {tuple(shape)} is needed")
+    return a
+
+
 def velocity_set(v=(1.0, 2.0, 3.0)):
     """(vx[19], vy[19]) of the discrete velocity model (Eq. 5)."""
     vv = np.asarray(v, dtype=np.float64)
@@ -160,7 +169,7 @@ def fixed_ghosts(p: Params, rho, ux, uy, T, cs: bool = False):
     """Fixed-equilibrium ghost values of Eq. (57) from the initial fields."""
     n = 2 * NQ * p.ny + 2 * NQ * p.nx
     out = np.zeros(n, dtype=_dt(cs))
-    a = [_arr(x, cs) for x in (rho, ux, uy, T)]
+    a = [_shaped(x, (p.ny, p.nx), cs) for x in (rho, ux, uy, T)]
     pc = p.c()
     lib(cs).oklb_fixed_ghosts(C.byref(pc), *[_ptr(x) for x in a], _ptr(out))
     return out
@@ -169,7 +178,7 @@ def fixed_ghosts(p: Params, rho, ux, uy, T, cs: bool = False):
 def init_feq(p: Params, rho, ux, uy, T, cs: bool = False):
     """f := f^(0) of the given fields [ny][nx]; returns f[19][ny][nx]."""
     f = np.zeros((NQ, p.ny, p.nx), dtype=_dt(cs))
-    a = [_arr(x, cs) for x in (rho, ux, uy, T)]
+    a = [_shaped(x, (p.ny, p.nx), cs) for x in (rho, ux, uy, T)]
     pc = p.c()
     lib(cs).oklb_init_feq(C.byref(pc), *[_ptr(x) for x in a], _ptr(f))
     return f
@@ -177,7 +186,7 @@ def init_feq(p: Params, rho, ux, uy, T, cs: bool = False):
 
 def fields(p: Params, f, cs: bool = False):
     """(rho, ux, uy, T) fields [ny][nx] of a distribution array."""
-    ff = _arr(f, cs)
+    ff = _shaped(f, (NQ, p.ny, p.nx), cs)
     outs = [np.zeros((p.ny, p.nx), dtype=_dt(cs)) for _ in range(4)]
     pc = p.c()
     lib(cs).oklb_fields(C.byref(pc), _ptr(ff), *[_ptr(o) for o in outs])
@@ -186,8 +195,8 @@ def fields(p: Params, f, cs: bool = False):
 
 def step(p: Params, f, fixed=None, cs: bool = False):
     """One time step (Eq. 47); returns the new f."""
-    ff = _arr(f, cs)
-    fx = _arr(fixed if fixed is not None else np.zeros(2 * NQ * (p.nx + p.ny)), cs)
+    ff = _shaped(f, (NQ, p.ny, p.nx), cs)
+    fx = _shaped(fixed if fixed is not None else np.zeros(2 * NQ * (p.nx + p.ny)), (2 * NQ * (p.nx + p.ny),), cs)
     out = np.empty_like(ff)
     pc = p.c()
     lib(cs).oklb_step(C.byref(pc), _ptr(ff), _ptr(fx), _ptr(out))
@@ -196,7 +205,7 @@ def step(p: Params, f, fixed=None, cs: bool = False):
 
 def diag(p: Params, f, cs: bool = False):
     """The seven diagnostics of one state (see oklb_diag)."""
-    ff = _arr(f, cs)
+    ff = _shaped(f, (NQ, p.ny, p.nx), cs)
     d = np.zeros(7, dtype=_dt(cs))
     pc = p.c()
     lib(cs).oklb_diag(C.byref(pc), _ptr(ff), _ptr(d))
@@ -205,7 +214,7 @@ def diag(p: Params, f, cs: bool = False):
 
 def mean_density(p: Params, f, cs: bool = False):
     """The averaged density profile rho_bar[ny] (see oklb_mean_density)."""
-    ff = _arr(f, cs)
+    ff = _shaped(f, (NQ, p.ny, p.nx), cs)
     out = np.zeros(p.ny, dtype=_dt(cs))
     pc = p.c()
     lib(cs).oklb_mean_density(C.byref(pc), _ptr(ff), _ptr(out))
@@ -214,8 +223,8 @@ def mean_density(p: Params, f, cs: bool = False):
 
 def run(p: Params, f, nsteps: int, fixed=None, sample_every: int = 0, cs: bool = False):
     """n steps from f; returns (f_final, diag[m][7])."""
-    ff = _arr(f, cs).copy()
-    fx = _arr(fixed if fixed is not None else np.zeros(2 * NQ * (p.nx + p.ny)), cs)
+    ff = _shaped(f, (NQ, p.ny, p.nx), cs).copy()
+    fx = _shaped(fixed if fixed is not None else np.zeros(2 * NQ * (p.nx + p.ny)), (2 * NQ * (p.nx + p.ny),), cs)
     cap = (nsteps // sample_every + 1) if sample_every > 0 else 0
     d = np.zeros((max(cap, 1), 7), dtype=_dt(cs))
     cnt = C.c_int64(0)

@@ -198,3 +198,20 @@ def test_ghost_nodes_by_explicit_padding(axis, bc):
     ref = core.step(pp, padded)
     ref = np.take(ref, np.arange(3, 3 + n), axis=ax)
     np.testing.assert_allclose(got, ref, rtol=1e-14, atol=1e-15)
+
+
+def test_wrapper_refuses_arrays_of_the_wrong_shape():
+    # the C code reads exactly the parameters' sizes: a mismatch is refused
+    # before the call instead of being read past
+    p = core.Params(nx=6, ny=5, dx=0.01, dy=0.01, dt=1e-4, tau=1e-4)
+    good = [np.ones((5, 6)) for _ in range(4)]
+    f = core.init_feq(p, *good)
+    with pytest.raises(ValueError):
+        core.init_feq(p, np.ones((4, 6)), *good[1:])
+    with pytest.raises(ValueError):
+        core.step(p, f[:, :4])
+    with pytest.raises(ValueError):
+        core.run(p, f, 1, fixed=np.zeros(5))
+    for fn in (core.fields, core.diag, core.mean_density):
+        with pytest.raises(ValueError):
+            fn(p, f[:18])
