@@ -8,6 +8,7 @@ library is newer than every source.
 from __future__ import annotations
 
 import concurrent.futures as cf
+import fcntl
 import glob
 import os
 import shutil
@@ -48,6 +49,16 @@ def build(force: bool = False, verbose: bool = False, extra: list | None = None)
     if not force and not _stale():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
+    # processes that start together (ranks of one job) build one at a time;
+    # the later ones find the library up to date
+    with open(os.path.join(BUILD, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        if not force and not _stale():
+            return LIB
+        return _build_locked(verbose, extra)
+
+
+def _build_locked(verbose: bool, extra: list | None) -> str:
     nvcc = _nvcc()
     extra = extra or []
 
