@@ -560,10 +560,13 @@ int klb_diagnostics(klb_t* h, double* out, int64_t cap, int64_t* count) {
     const int64_t avail = std::min<int64_t>(ns, h->cap);
     const int64_t m = std::min<int64_t>(avail, cap);
     const int64_t first = ns - avail;  // oldest retained sample
-    for (int64_t i = 0; i < m; ++i) {
+    // the retained samples in ring order: at most two contiguous runs of slots
+    for (int64_t i = 0; i < m;) {
         const int64_t slot = (first + i) % h->cap;
-        CK(h, cudaMemcpyAsync(out + 7 * i, h->diag_ring + 7 * slot, 7 * sizeof(double), cudaMemcpyDeviceToHost,
-                              h->stream));
+        const int64_t run = std::min<int64_t>(m - i, h->cap - slot);
+        CK(h, cudaMemcpyAsync(out + 7 * i, h->diag_ring + 7 * slot, 7 * run * sizeof(double),
+                              cudaMemcpyDeviceToHost, h->stream));
+        i += run;
     }
     *count = m;
     return klb_sync(h);

@@ -70,6 +70,12 @@ def test_create_rejects_bad_params_without_gpu(lib):
     with pytest.raises(klb.KlbError) as e:
         klb.Klb(p)
     assert e.value.code == -1
+    # an empty grid and non-positive step sizes
+    for args in ((8, 0, 0.01, 0.01, 1e-5, 1e-5), (8, 8, 0.01, 0.01, 0.0, 1e-5), (8, 8, 0.01, 0.01, 1e-5, -1.0),
+                 (8, 8, 0.0, 0.01, 1e-5, 1e-5)):
+        with pytest.raises(klb.KlbError) as e:
+            klb.Klb(klb.make_params(*args))
+        assert e.value.code == -1, args
 
 
 def test_scheme_validation_without_gpu(lib):

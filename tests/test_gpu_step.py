@@ -299,6 +299,45 @@ def test_step_before_init_and_bad_args():
         assert e.value.code == -1
 
 
+def test_zero_steps_and_empty_series():
+    # zero steps enqueue nothing and leave the state, the step count and the
+    # (unsampled) diagnostics series as they are; an empty batch is refused
+    pb = _problem(16, 12, "periodic", "outflow")
+    for prec in ("fp32", "fp64"):
+        with gpu_handle(pb, prec, sample_every=0) as h:
+            h.init_fields(*inputs.smooth_random_fields(16, 12, 1))
+            f0, n0 = h.get_f(), h.launch_count
+            h.step(0)
+            h.sync()
+            assert h.launch_count == n0 and h.step_count == 0
+            assert np.array_equal(h.get_f(), f0)
+            assert h.diagnostics().shape == (0, 7)
+    with klb.KlbBatch.from_problems([pb]) as b:
+        b.members[0].init_fields(*inputs.smooth_random_fields(16, 12, 1))
+        b.step(0)
+        b.sync()
+        assert b.members[0].step_count == 0
+    with pytest.raises((klb.KlbError, ValueError)):
+        klb.KlbBatch([])
+
+
+def test_diagnostics_ring_keeps_the_latest_samples():
+    # a ring of 5 samples after 11 samples (every 2 of 20 steps) holds the last
+    # 5, bitwise those of a large ring, and returns them oldest first (the copy
+    # runs across the ring's wrap); asking for 3 gives the oldest 3 of them
+    pb = _problem(20, 14, "periodic", "outflow")
+    fields = inputs.smooth_random_fields(20, 14, 4)
+    series = {}
+    for cap in (5, 64):
+        with gpu_handle(pb, "fp32", sample_every=2, diag_capacity=cap) as h:
+            h.init_fields(*fields)
+            h.step(20)
+            series[cap] = (h.diagnostics(), h.diagnostics(cap=3))
+    assert series[64][0].shape == (11, 7) and series[5][0].shape == (5, 7)
+    assert np.array_equal(series[5][0], series[64][0][-5:])
+    assert np.array_equal(series[5][1], series[64][0][-5:-2])
+
+
 def test_bounded_wait_runs_out_and_context_survives():
     # fault injection from the host: the step kernel also waits on a barrier
     # nothing arrives on, with a short poll budget; the wait runs out, the
