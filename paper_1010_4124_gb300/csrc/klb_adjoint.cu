@@ -217,16 +217,7 @@ int klb_adjoint_create(const klb_params* p, int64_t nsteps, int32_t checkpoint_e
         delete a;
         return afail(nullptr, r, std::string("forward grid: ") + klb_last_error(nullptr));
     }
-    klb_t* h = a->h;
-    if (q.precision == KLB_FP32) {
-        // a grid with fewer 16-row tiles than two per SM steps faster with
-        // 8-row tiles (two CTAs per SM); both give the same bits
-        int dev = 0, sms = 1, tiles_x = 0, ntiles = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        f32_tiles(h->g.nx, h->g.ny, 0, &tiles_x, &ntiles);
-        if (ntiles < 2 * sms) klb_set_variant(h, 1);
-    }
+    klb_t* h = a->h;  // an FP32 grid starts with the tile shape faster for its size
     const size_t sb = state_bytes(h);
     const size_t nn = (size_t)h->g.nx * h->g.ny;
     bool ok = true;

@@ -245,6 +245,9 @@ int klb_batch_create(const klb_params* ps, int n, klb_batch_t** out) {
         int r = klb_create(&p, &h);
         if (r != KLB_OK) return cleanup(r, std::string("member ") + std::to_string(i) + ": " + klb_last_error(nullptr));
         b->m.push_back(h);
+        // one launch steps all members: their tensor maps must have the batch's tile shape
+        if (h->variant != b->variant && klb_set_variant(h, b->variant) != KLB_OK)
+            return cleanup(KLB_E_CUDA, std::string("member ") + std::to_string(i) + ": " + h->err);
         if (p.sample_every > 0) period = period / gcd64(period, p.sample_every) * p.sample_every;
     }
     b->period = (int)std::min<int64_t>(period, 1 << 20);

@@ -224,6 +224,7 @@ int klb_create(const klb_params* pin, klb_t** out) {
         h->nparts = std::max(f32_grid(p.nx, p.ny, 0), f32_grid(p.nx, p.ny, 1));
     }
     h->cap = p.diag_capacity > 0 ? p.diag_capacity : 4096;
+    h->variant = p.precision == KLB_FP32 ? f32_default_variant(p.nx, p.ny) : 0;
 
     auto cleanup = [&](int code) {
         klb_destroy(h);

@@ -27,6 +27,7 @@ void f64_tile(int* tx, int* ty);
 // of diagnostics partial records); f32_box = the TMA box of one tile.
 void f32_tiles(int nx, int ny, int variant, int* tiles_x, int* ntiles);
 int f32_grid(int nx, int ny, int variant);
+int f32_default_variant(int nx, int ny);  // the tile shape a new FP32 handle starts with
 void f32_box(int variant, unsigned* bx, unsigned* by, unsigned* bz);
 // Descriptor of one grid for the FP32 step: the TMA map of its current state,
 // the buffer that receives the next one, its geometry and the index of its
