@@ -117,3 +117,15 @@ def test_binding_refuses_arrays_of_the_wrong_size():
     assert klb._ptr(t, 20) == (t.data_ptr(), 0)
     with pytest.raises(ValueError):
         klb._ptr(t, 19)
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    # the product path has no fallback: without the CUDA library every call
+    # raises (nothing is computed on the CPU)
+    from paper_1010_4124_gb300 import klb
+    monkeypatch.setattr(klb, "_lib", None)
+    monkeypatch.setattr(klb, "LIB_PATH", str(tmp_path / "libklb.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        klb.lib()
+    with pytest.raises(RuntimeError):
+        klb.Klb(klb.make_params(8, 8, 0.01, 0.01, 1e-5, 1e-5))
