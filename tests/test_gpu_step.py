@@ -436,6 +436,19 @@ def test_khi512_growth_rate_matches_oracle(prec):
             assert np.abs(d[:, k] - dref[:, k]).max() <= 1e-12 * scale, k
 
 
+def test_fp32_default_tile_shape_by_size():
+    # a new FP32 handle starts with the shape measured faster for its size:
+    # 8-row tiles while the grid has at most 40 sixteen-row tiles per SM
+    torch = pytest.importorskip("torch")
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    for nx, ny in ((256, 256), (1024, 512), (2048, 1024), (2048, 2048), (4096, 4096)):
+        tiles16 = ((nx + 4 + 31) // 32) * ((ny + 15) // 16)
+        with gpu_handle(inputs.khi(nx, ny, 1), "fp32") as h:
+            assert h.variant == (1 if tiles16 <= 40 * sms else 0), (nx, ny, h.variant)
+    with gpu_handle(inputs.khi(64, 64, 1), "fp64") as h:
+        assert h.variant == 0
+
+
 def test_fp32_variants_are_bitwise_identical():
     # the two tile shapes of the FP32 kernel compute every node with the same
     # arithmetic: the states agree bit for bit
