@@ -449,10 +449,12 @@ def test_fp32_default_tile_shape_by_size():
         assert h.variant == 0
 
 
-def test_fp32_variants_are_bitwise_identical():
+@pytest.mark.parametrize("bcx,bcy", [("periodic", "outflow"), ("outflow", "fixed_eq")])
+def test_fp32_variants_are_bitwise_identical(bcx, bcy):
     # the two tile shapes of the FP32 kernel compute every node with the same
-    # arithmetic: the states agree bit for bit
-    pb = inputs.khi(300, 170, 30)
+    # arithmetic: the states agree bit for bit (ghost images and fixed ghosts
+    # included)
+    pb = inputs.khi(300, 170, 30).with_(bc_x=(bcx, bcx), bc_y=(bcy, bcy))
     fields = inputs.fields(pb)
     out = []
     for v in (0, 1):
