@@ -192,8 +192,9 @@ struct ArithF32 {
         const T p1 = __fmul_rn(s1, s1), p2 = __fmul_rn(s2, s2), p3 = __fmul_rn(s3, s3);
         const T P23 = __fmul_rn(p2, p3), P13 = __fmul_rn(p1, p3), P12 = __fmul_rn(p1, p2);
         const T G1 = fmaf(0.5f / 6.f, d2, __fmul_rn(-0.2f / 6.f, d1));
-        const T G2 = fmaf(1.2f / 6.f, d3, __fmul_rn(0.1f, d2));
-        const T G3 = fmaf(1.2f / 6.f, d3, __fmul_rn(0.05f, e4));
+        const T t3 = __fmul_rn(1.2f / 6.f, d3);  // shared by G2 and G3
+        const T G2 = fmaf(0.1f, d2, t3);
+        const T G3 = fmaf(0.05f, e4, t3);
         const T num = fmaf(G1, P23, fmaf(G2, P13, __fmul_rn(G3, P12)));
         const T den = fmaf(0.1f, P23, fmaf(0.6f, P13, __fmul_rn(0.3f, P12)));
         return fmaf(num, rcp_approx(den), c);
@@ -214,8 +215,9 @@ struct ArithF32 {
         const float2 P23 = __fmul2_rn(p2, p3), P13 = __fmul2_rn(p1, p3), P12 = __fmul2_rn(p1, p2);
         // (delta_1/6)(5 D2 - 2 D1), (delta_2/6)(D2 + 2 D3), (delta_3/6)(4 D3 + e4)
         const float2 G1 = __ffma2_rn(make_float2(0.5f / 6.f, 0.5f / 6.f), d2, __fmul2_rn(make_float2(-0.2f / 6.f, -0.2f / 6.f), d1));
-        const float2 G2 = __ffma2_rn(make_float2(1.2f / 6.f, 1.2f / 6.f), d3, __fmul2_rn(make_float2(0.1f, 0.1f), d2));
-        const float2 G3 = __ffma2_rn(make_float2(1.2f / 6.f, 1.2f / 6.f), d3, __fmul2_rn(make_float2(0.05f, 0.05f), e4));
+        const float2 t3 = __fmul2_rn(make_float2(1.2f / 6.f, 1.2f / 6.f), d3);
+        const float2 G2 = __ffma2_rn(make_float2(0.1f, 0.1f), d2, t3);
+        const float2 G3 = __ffma2_rn(make_float2(0.05f, 0.05f), e4, t3);
         const float2 num = __ffma2_rn(G1, P23, __ffma2_rn(G2, P13, __fmul2_rn(G3, P12)));
         const float2 den = __ffma2_rn(make_float2(0.1f, 0.1f), P23,
                                       __ffma2_rn(make_float2(0.6f, 0.6f), P13, __fmul2_rn(make_float2(0.3f, 0.3f), P12)));
