@@ -57,3 +57,26 @@ def test_mixing_layer_thickens():
             md = h.mean_density()
             widths.append(int(((md > lo) & (md < hi)).sum()))
     assert all(b > a for a, b in zip(widths, widths[1:])), widths
+
+
+def test_fp32_sod_converges_to_the_exact_solution():
+    # Sec. III.B: the Sod tube (gamma = 2, R8) on the FP32 production path at
+    # 100, 200 and 400 cells, t = 0.1 (dt scaled with dx): the L1 errors of
+    # rho, u, p and T against the exact Riemann solution shrink under
+    # refinement and stay below 0.02 at 200 cells
+    from oracle import riemann
+    left, right = (1.0, 0.0, 1.0), (0.125, 0.0, 0.1)
+    errs = {}
+    for nx in (100, 200, 400):
+        pb = inputs.sod(nx=nx, ny=4, steps=int(round(0.1 / (2e-5 * 200 / nx))))
+        with klb.Klb.from_problem(pb, precision="fp32", sample_every=0) as h:
+            h.init_fields(*inputs.fields(pb))
+            h.step(pb.steps)
+            r, u, w, T = (a[0] for a in h.moments())
+        x = (np.arange(nx) + 0.5) * pb.dx
+        re, ue, pe = riemann.sample(x, pb.steps * pb.dt, 0.5, left, right, gamma=2.0)
+        errs[nx] = [float(np.abs(a - b).mean()) for a, b in ((r, re), (u, ue), (r * T, pe), (T, pe / re))]
+    print("FP32 Sod L1 (rho, u, p, T):", errs)
+    for k in range(4):
+        assert errs[200][k] < errs[100][k] and errs[400][k] < errs[200][k], errs
+    assert max(errs[200]) < 0.02, errs
