@@ -259,7 +259,7 @@ int klb_batch_create(const klb_params* ps, int n, klb_batch_t** out) {
         cudaGetLastError();
         return cleanup(KLB_E_NOMEM, "cudaMalloc of the batch descriptors failed");
     }
-    cudaMemset(b->err_dev, 0, sizeof(int));
+    if (cudaMemset(b->err_dev, 0, sizeof(int)) != cudaSuccess) return cleanup(KLB_E_CUDA, "cudaMemset failed");
     if (upload(b) != KLB_OK) return cleanup(KLB_E_CUDA, b->err);
     *out = b;
     return KLB_OK;
@@ -401,25 +401,30 @@ int klb_batch_autotune(klb_batch_t* b, int steps, int* variant) {
             }
             p = 1 - p;
         }
-        cudaEventRecord(e1, b->stream);
-        cudaEventSynchronize(e1);
         float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
+        cudaError_t et = cudaEventRecord(e1, b->stream);
+        if (et == cudaSuccess) et = cudaEventSynchronize(e1);
+        if (et == cudaSuccess) et = cudaEventElapsedTime(&ms, e0, e1);
+        if (et != cudaSuccess && r == KLB_OK)
+            r = bfail(b, KLB_E_CUDA, std::string("autotune timing: ") + cudaGetErrorString(et));
         if (r == KLB_OK && (best_ms < 0.f || ms < best_ms)) {
             best_ms = ms;
             best = v;
         }
-        // restore the state for the next trial
+        // restore the state for the next trial (and for the run after the last one)
         for (size_t i = 0; i < b->m.size(); ++i) {
             klb_t* h = b->m[i];
-            cudaMemcpyAsync(h->buf[p0], snap[i], (size_t)NQ * h->g.plane * h->esize, cudaMemcpyDeviceToDevice,
-                            b->stream);
+            cudaError_t ec = cudaMemcpyAsync(h->buf[p0], snap[i], (size_t)NQ * h->g.plane * h->esize,
+                                             cudaMemcpyDeviceToDevice, b->stream);
+            if (ec != cudaSuccess && r == KLB_OK)
+                r = bfail(b, KLB_E_CUDA, std::string("autotune restore: ") + cudaGetErrorString(ec));
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaStreamSynchronize(b->stream);
+    const cudaError_t es = cudaStreamSynchronize(b->stream);
     release();
+    if (es != cudaSuccess && r == KLB_OK) r = bfail(b, KLB_E_CUDA, std::string("autotune: ") + cudaGetErrorString(es));
     if (r != KLB_OK) return r;
     r = klb_batch_set_variant(b, best);
     if (r == KLB_OK && variant) *variant = best;

@@ -252,8 +252,11 @@ int klb_create(const klb_params* pin, klb_t** out) {
         fail(nullptr, KLB_E_NOMEM, "cudaMalloc of the staging buffers failed");
         return cleanup(KLB_E_NOMEM);
     }
-    cudaMemset(h->err_dev, 0, sizeof(int));
-    cudaMemset(h->nsamp_dev, 0, sizeof(long long));
+    if (cudaMemset(h->err_dev, 0, sizeof(int)) != cudaSuccess ||
+        cudaMemset(h->nsamp_dev, 0, sizeof(long long)) != cudaSuccess) {
+        fail(nullptr, KLB_E_CUDA, "cudaMemset failed");
+        return cleanup(KLB_E_CUDA);
+    }
     if (p.stream) {
         h->stream = (cudaStream_t)p.stream;
     } else {
