@@ -170,33 +170,39 @@ struct ArithF32 {
     // Since every term scales with v except the absolute epsilon,
     // h(v f; eps) = v h(f; eps / v^2): the factor v sits in the update.
     __device__ __forceinline__ static T weno(T a, T b, T c, T d, T e, T eps) {
-        // With the differences of neighbouring values D1 = b - a, D2 = c - b,
-        // D3 = d - c and e4 = d - e, the smoothness indicators of
+        // With the differences of neighbouring values D1 = a - b (sign flipped),
+        // D2 = c - b, D3 = d - c and e4 = d - e, the smoothness indicators of
         // Eqs. (53)-(55), scaled by 3/4, read
-        //   s_1 = D1 (D1 - 11/4 D2) + 5/2 D2^2,
+        //   s_1 = D1 (D1 + 11/4 D2) + 5/2 D2^2,
         //   s_2 = D2 (D2 - 5/4 D3) + D3^2,
         //   s_3 = e4 (e4 + 11/4 D3) + 5/2 D3^2,
         // and eps (the constant passed in) is scaled by 3/4 as well: the
         // common factor cancels in the weights.  The candidates of Eqs. (49)-(51)
-        // relative to c read h_1 - c = (5 D2 - 2 D1)/6, h_2 - c = (D2 + 2 D3)/6,
+        // relative to c read h_1 - c = (5 D2 + 2 D1)/6, h_2 - c = (D2 + 2 D3)/6,
         // h_3 - c = (4 D3 + e4)/6; with the optimal weights delta_q and the 1/6
-        // folded in, h = c + sum_q G_q P_q / sum_q delta_q P_q.
+        // folded in, and numerator and denominator both scaled by 10 (their
+        // ratio is unchanged),
+        //   h = c + (G1 P23 + G2 P13 + G3 P12) / (P23 + 6 P13 + 3 P12),
+        //   G1 = 5/6 D2 + 1/3 D1, G2 = D2 + 2 D3, G3 = 2 D3 + e4 / 2,
+        // with P the products of the other two (eps + sigma)^2.  The sign of D1
+        // and the common factor 10 let the packed form use few distinct
+        // constant pairs (each costs a register pair or a reload).
         // Every operation is an explicitly rounded multiply, add or fused
         // multiply-add, in the same order as each lane of weno2(), so the
         // scalar and packed evaluations give the same bits.
-        const T d1 = fmaf(a, -1.f, b), d2 = fmaf(b, -1.f, c), d3 = fmaf(c, -1.f, d), e4 = fmaf(e, -1.f, d);
+        const T d1 = fmaf(b, -1.f, a), d2 = fmaf(b, -1.f, c), d3 = fmaf(c, -1.f, d), e4 = fmaf(e, -1.f, d);
         const T a2 = __fmul_rn(d2, d2), a3 = __fmul_rn(d3, d3);
-        const T s1 = fmaf(d1, fmaf(-2.75f, d2, d1), fmaf(2.5f, a2, eps));
+        const T s1 = fmaf(d1, fmaf(2.75f, d2, d1), fmaf(2.5f, a2, eps));
         const T s2 = fmaf(d2, fmaf(-1.25f, d3, d2), fmaf(d3, d3, eps));
         const T s3 = fmaf(e4, fmaf(2.75f, d3, e4), fmaf(2.5f, a3, eps));
         const T p1 = __fmul_rn(s1, s1), p2 = __fmul_rn(s2, s2), p3 = __fmul_rn(s3, s3);
         const T P23 = __fmul_rn(p2, p3), P13 = __fmul_rn(p1, p3), P12 = __fmul_rn(p1, p2);
-        const T G1 = fmaf(0.5f / 6.f, d2, __fmul_rn(-0.2f / 6.f, d1));
-        const T t3 = __fmul_rn(1.2f / 6.f, d3);  // shared by G2 and G3
-        const T G2 = fmaf(0.1f, d2, t3);
-        const T G3 = fmaf(0.05f, e4, t3);
+        const T G1 = fmaf(5.f / 6.f, d2, __fmul_rn(1.f / 3.f, d1));
+        const T t3 = __fadd_rn(d3, d3);  // 2 D3, shared by G2 and G3
+        const T G2 = __fadd_rn(d2, t3);
+        const T G3 = fmaf(0.5f, e4, t3);
         const T num = fmaf(G1, P23, fmaf(G2, P13, __fmul_rn(G3, P12)));
-        const T den = fmaf(0.1f, P23, fmaf(0.6f, P13, __fmul_rn(0.3f, P12)));
+        const T den = fmaf(6.f, P13, fmaf(3.f, P12, P23));
         return fmaf(num, rcp_approx(den), c);
     }
     // The same flux for two independent faces at once (packed f32x2
@@ -204,23 +210,22 @@ struct ArithF32 {
     __device__ __forceinline__ static float2 weno2(float2 a, float2 b, float2 c, float2 d, float2 e, float2 eps) {
         // lane by lane the same operations as weno()
         const float2 m1 = make_float2(-1.f, -1.f);
-        const float2 d1 = __ffma2_rn(a, m1, b), d2 = __ffma2_rn(b, m1, c);
+        const float2 d1 = __ffma2_rn(b, m1, a), d2 = __ffma2_rn(b, m1, c);
         const float2 d3 = __ffma2_rn(c, m1, d), e4 = __ffma2_rn(e, m1, d);
         const float2 a2 = __fmul2_rn(d2, d2), a3 = __fmul2_rn(d3, d3);
-        const float2 k25 = make_float2(2.5f, 2.5f);
-        const float2 s1 = __ffma2_rn(d1, __ffma2_rn(make_float2(-2.75f, -2.75f), d2, d1), __ffma2_rn(k25, a2, eps));
+        const float2 k25 = make_float2(2.5f, 2.5f), k275 = make_float2(2.75f, 2.75f);
+        const float2 s1 = __ffma2_rn(d1, __ffma2_rn(k275, d2, d1), __ffma2_rn(k25, a2, eps));
         const float2 s2 = __ffma2_rn(d2, __ffma2_rn(make_float2(-1.25f, -1.25f), d3, d2), __ffma2_rn(d3, d3, eps));
-        const float2 s3 = __ffma2_rn(e4, __ffma2_rn(make_float2(2.75f, 2.75f), d3, e4), __ffma2_rn(k25, a3, eps));
+        const float2 s3 = __ffma2_rn(e4, __ffma2_rn(k275, d3, e4), __ffma2_rn(k25, a3, eps));
         const float2 p1 = __fmul2_rn(s1, s1), p2 = __fmul2_rn(s2, s2), p3 = __fmul2_rn(s3, s3);
         const float2 P23 = __fmul2_rn(p2, p3), P13 = __fmul2_rn(p1, p3), P12 = __fmul2_rn(p1, p2);
-        // (delta_1/6)(5 D2 - 2 D1), (delta_2/6)(D2 + 2 D3), (delta_3/6)(4 D3 + e4)
-        const float2 G1 = __ffma2_rn(make_float2(0.5f / 6.f, 0.5f / 6.f), d2, __fmul2_rn(make_float2(-0.2f / 6.f, -0.2f / 6.f), d1));
-        const float2 t3 = __fmul2_rn(make_float2(1.2f / 6.f, 1.2f / 6.f), d3);
-        const float2 G2 = __ffma2_rn(make_float2(0.1f, 0.1f), d2, t3);
-        const float2 G3 = __ffma2_rn(make_float2(0.05f, 0.05f), e4, t3);
+        const float2 G1 = __ffma2_rn(make_float2(5.f / 6.f, 5.f / 6.f), d2,
+                                     __fmul2_rn(make_float2(1.f / 3.f, 1.f / 3.f), d1));
+        const float2 t3 = __fadd2_rn(d3, d3);
+        const float2 G2 = __fadd2_rn(d2, t3);
+        const float2 G3 = __ffma2_rn(make_float2(0.5f, 0.5f), e4, t3);
         const float2 num = __ffma2_rn(G1, P23, __ffma2_rn(G2, P13, __fmul2_rn(G3, P12)));
-        const float2 den = __ffma2_rn(make_float2(0.1f, 0.1f), P23,
-                                      __ffma2_rn(make_float2(0.6f, 0.6f), P13, __fmul2_rn(make_float2(0.3f, 0.3f), P12)));
+        const float2 den = __ffma2_rn(make_float2(6.f, 6.f), P13, __ffma2_rn(make_float2(3.f, 3.f), P12, P23));
         const float2 r = make_float2(rcp_approx(den.x), rcp_approx(den.y));
         return __ffma2_rn(num, r, c);
     }

@@ -112,8 +112,14 @@ def test_fp32_khi_fields_1000_steps():
     assert max(errs["rho"], errs["u"], errs["T"]) <= 1e-4, errs
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-4)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
 def test_diagnostics_series_parity(prec, tol):
+    # tol is the field bar (relative to the field's max norm); the sums of
+    # mass, momentum and energy (columns 0-3) are held to it.  Columns 4-6 are
+    # built from u_y alone (max |u_y|, max and sum of rho u_y^2 / 2): an error
+    # of tol max|u| in u_y is tol max|u| / max|u_y| of max |u_y| and twice that
+    # of rho u_y^2 / 2 -- about 2.5e-4 and 5e-4 here in FP32 (max|u| = 0.25,
+    # max |u_y| >= 0.0099 over the series)
     pb = inputs.khi(64, 96, 200, Dv=4.0, Drho=4.0, sample_every=10)
     p = oracle_params(pb)
     fields = inputs.fields(pb)
@@ -124,11 +130,14 @@ def test_diagnostics_series_parity(prec, tol):
         h.step(pb.steps)
         d = h.diagnostics()
     assert d.shape == dref.shape == (21, 7)
+    umax = np.abs(fields[1]).max()
+    uy_over_u = dref[:, 4].min() / umax  # the smallest max|u_y| of the series against max|u|
     for k in range(7):
         scale = np.abs(dref[:, k]).max()
         if k in (1, 2):  # momentum sums cancel to ~0: compare against the mass scale
             scale = np.abs(dref[:, 0]).max()
-        assert np.abs(d[:, k] - dref[:, k]).max() <= tol * scale, k
+        bound = tol if k <= 3 else (tol / uy_over_u if k == 4 else 2 * tol / uy_over_u)
+        assert np.abs(d[:, k] - dref[:, k]).max() <= bound * scale, (k, bound)
 
 
 @pytest.mark.parametrize("variant", [0, 1])
