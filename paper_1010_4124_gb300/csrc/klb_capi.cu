@@ -56,6 +56,23 @@ static void fill_const(const klb_params& p, StepConst<T>& c) {
         c.ex[q] = vx != 0 ? T(0.75 * eps / (vx * vx)) : T(0);
         c.ey[q] = vy != 0 ? T(0.75 * eps / (vy * vy)) : T(0);
     }
+    for (int q = 0; q < NQ; ++q) {
+        c.epair[q][0] = c.ex[q];
+        c.epair[q][1] = c.ey[q];
+    }
+    for (int m = 0; m < 3; ++m) {
+        c.epair[19 + m][0] = c.ex[6 * m + 3];
+        c.epair[19 + m][1] = c.ex[6 * m + 6];
+    }
+    {
+        int ys[12], n = 0;  // the velocities with v_y != 0 in slot order
+        for (int q = 1; q < NQ; ++q)
+            if ((q - 1) % 3 != 2) ys[n++] = q;
+        for (int k = 0; k < 6; ++k) {
+            c.epair[22 + k][0] = c.ey[ys[2 * k]];
+            c.epair[22 + k][1] = c.ey[ys[2 * k + 1]];
+        }
+    }
     // F_k(T) = T [a_{k+1} a_{k+2} - 4 (a_{k+1} + a_{k+2}) T + 24 T^2] / [3 a_k (a_k - a_{k+1})(a_k - a_{k+2})]
     for (int k = 0; k < 3; ++k) {
         const double ak = p.v[k] * p.v[k];

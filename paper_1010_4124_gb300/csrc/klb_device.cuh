@@ -43,6 +43,10 @@ struct StepConst {
     // FP32 path
     T cx[NQ], cy[NQ];  // dt * v_qx / dx, dt * v_qy / dy
     T ex[NQ], ey[NQ];  // FP32 WENO: (3/4) eps / v_qx^2, (3/4) eps / v_qy^2 (unscaled plane, sigma scaled by 3/4)
+    // the same as the pairs the packed WENO5 evaluations take, one 8-byte load
+    // each: [q] = (ex, ey) of velocity q; [19 + m] = (ex, ex) of the x-only
+    // velocities 6m + 3 and 6m + 6; [22 + k] = (ey, ey) of y slots 2k and 2k + 1
+    alignas(8) T epair[28][2];
     T fk[3][3];        // F_k(T) = T (fk[k][0] + T (fk[k][1] + T fk[k][2])), k = 1..3
     T ginv[4][4];      // inverse Gram matrix of the collision invariants (1, v_x, v_y, |v|^2)
     // FP64 path (the paper's formulas term by term)

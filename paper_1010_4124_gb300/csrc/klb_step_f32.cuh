@@ -102,6 +102,11 @@ __device__ __forceinline__ void yst(const float* P, int r, int s, float v[5]) {
         v[0] = a[2 * S]; v[1] = a[S]; v[2] = a[0]; v[3] = a[-S]; v[4] = a[-2 * S];
     }
 }
+// entry i of the epsilon pairs of the step constants, as one 8-byte load
+__device__ __forceinline__ float2 eps_pair(const StepConst<float>& c, int i) {
+    return *reinterpret_cast<const float2*>(c.epair[i]);
+}
+
 // The flux of the convection scheme SCH (0 WENO5, Eqs. 48-55; 1 first-order
 // upwind; 2 second-order upwind; 3 second-order TVD) from five upwind-ordered
 // stencil values of the unscaled plane, for two faces at once (packed) and
@@ -109,10 +114,10 @@ __device__ __forceinline__ void yst(const float* P, int r, int s, float v[5]) {
 // factor v of F = v f stays in the update constants as for WENO5.  The
 // scalar form performs each lane's operations of the packed one.
 template <int SCH>
-__device__ __forceinline__ float2 face_pair(const float u[5], const float w[5], float eu, float ew) {
+__device__ __forceinline__ float2 face_pair(const float u[5], const float w[5], float2 e) {
     const float2 b = make_float2(u[1], w[1]), c = make_float2(u[2], w[2]), d = make_float2(u[3], w[3]);
     if constexpr (SCH == 0) {
-        return ArithF32::weno2(make_float2(u[0], w[0]), b, c, d, make_float2(u[4], w[4]), make_float2(eu, ew));
+        return ArithF32::weno2(make_float2(u[0], w[0]), b, c, d, make_float2(u[4], w[4]), e);
     } else if constexpr (SCH == 1) {
         return c;
     } else {
@@ -163,7 +168,7 @@ __device__ __forceinline__ void pass_a_xy(const StepConst<float>& c, const float
     float u[5], w[5];
     xst<SGX>(P, r, s, u);
     yst<SGY>(P, r, s, w);
-    const float2 h = face_pair<SCH>(u, w, c.ex[Q], c.ey[Q]);
+    const float2 h = face_pair<SCH>(u, w, eps_pair(c, Q));
     float hr = __shfl_down_sync(0xffffffffu, h.x, 1);
     if (lane == 31) hr = edge[Q - 1];  // the tile's right edge face
     post[Q] = fmaf(-c.cx[Q], __fsub_rn(hr, h.x), post[Q]);
@@ -178,7 +183,8 @@ __device__ __forceinline__ void pass_a_xx(const StepConst<float>& c, const float
     float u[5], w[5];
     xst<sgn_x(QA)>(tile + QA * v3::Shape<TY>::PLANE, r, s, u);
     xst<sgn_x(QB)>(tile + QB * v3::Shape<TY>::PLANE, r, s, w);
-    const float2 h = face_pair<SCH>(u, w, c.ex[QA], c.ex[QB]);
+    static_assert(QB == QA + 3 && (QA - 3) % 6 == 0, "x-only pairs (6m + 3, 6m + 6)");
+    const float2 h = face_pair<SCH>(u, w, eps_pair(c, 19 + (QA - 3) / 6));
     float ra = __shfl_down_sync(0xffffffffu, h.x, 1);
     float rb = __shfl_down_sync(0xffffffffu, h.y, 1);
     if (lane == 31) {  // the tile's right edge faces
@@ -198,7 +204,7 @@ __device__ __forceinline__ void top_face_pair(const StepConst<float>& c, const f
     float u[5], w[5];
     yst<sgn_y(QA)>(tile + QA * v3::Shape<TY>::PLANE, TY + 3, s, u);
     yst<sgn_y(QB)>(tile + QB * v3::Shape<TY>::PLANE, TY + 3, s, w);
-    const float2 h = face_pair<SCH>(u, w, c.ey[QA], c.ey[QB]);
+    const float2 h = face_pair<SCH>(u, w, eps_pair(c, 22 + K / 2));
     yf[(K * (TY + 1) + TY) * 32 + lane] = h.x;
     yf[((K + 1) * (TY + 1) + TY) * 32 + lane] = h.y;
 }
