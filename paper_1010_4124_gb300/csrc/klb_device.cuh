@@ -89,6 +89,12 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
+// the constant pairs of the packed WENO5 flux: -1, 5/2, 11/4, -5/4, 5/6, 1/3,
+// 1/2, 6, 3 (both lanes alike; see ArithF32::weno)
+static __constant__ float2 kWenoPairs[9] = {{-1.f, -1.f}, {2.5f, 2.5f}, {2.75f, 2.75f}, {-1.25f, -1.25f},
+                                            {5.f / 6.f, 5.f / 6.f}, {1.f / 3.f, 1.f / 3.f}, {0.5f, 0.5f},
+                                            {6.f, 6.f}, {3.f, 3.f}};
+
 // ===========================================================================
 // FP32 production arithmetic.  Every operation is written as an explicitly
 // rounded multiply, add or fused multiply-add, so that the compiler cannot
@@ -210,26 +216,26 @@ struct ArithF32 {
         return fmaf(num, rcp_approx(den), c);
     }
     // The same flux for two independent faces at once (packed f32x2
-    // arithmetic: one instruction for both lanes of the pair).
+    // arithmetic: one instruction for both lanes of the pair).  Its constant
+    // pairs come from constant memory (kWenoPairs).
     __device__ __forceinline__ static float2 weno2(float2 a, float2 b, float2 c, float2 d, float2 e, float2 eps) {
         // lane by lane the same operations as weno()
-        const float2 m1 = make_float2(-1.f, -1.f);
+        const float2 m1 = kWenoPairs[0];
         const float2 d1 = __ffma2_rn(b, m1, a), d2 = __ffma2_rn(b, m1, c);
         const float2 d3 = __ffma2_rn(c, m1, d), e4 = __ffma2_rn(e, m1, d);
         const float2 a2 = __fmul2_rn(d2, d2), a3 = __fmul2_rn(d3, d3);
-        const float2 k25 = make_float2(2.5f, 2.5f), k275 = make_float2(2.75f, 2.75f);
+        const float2 k25 = kWenoPairs[1], k275 = kWenoPairs[2];
         const float2 s1 = __ffma2_rn(d1, __ffma2_rn(k275, d2, d1), __ffma2_rn(k25, a2, eps));
-        const float2 s2 = __ffma2_rn(d2, __ffma2_rn(make_float2(-1.25f, -1.25f), d3, d2), __ffma2_rn(d3, d3, eps));
+        const float2 s2 = __ffma2_rn(d2, __ffma2_rn(kWenoPairs[3], d3, d2), __ffma2_rn(d3, d3, eps));
         const float2 s3 = __ffma2_rn(e4, __ffma2_rn(k275, d3, e4), __ffma2_rn(k25, a3, eps));
         const float2 p1 = __fmul2_rn(s1, s1), p2 = __fmul2_rn(s2, s2), p3 = __fmul2_rn(s3, s3);
         const float2 P23 = __fmul2_rn(p2, p3), P13 = __fmul2_rn(p1, p3), P12 = __fmul2_rn(p1, p2);
-        const float2 G1 = __ffma2_rn(make_float2(5.f / 6.f, 5.f / 6.f), d2,
-                                     __fmul2_rn(make_float2(1.f / 3.f, 1.f / 3.f), d1));
+        const float2 G1 = __ffma2_rn(kWenoPairs[4], d2, __fmul2_rn(kWenoPairs[5], d1));
         const float2 t3 = __fadd2_rn(d3, d3);
         const float2 G2 = __fadd2_rn(d2, t3);
-        const float2 G3 = __ffma2_rn(make_float2(0.5f, 0.5f), e4, t3);
+        const float2 G3 = __ffma2_rn(kWenoPairs[6], e4, t3);
         const float2 num = __ffma2_rn(G1, P23, __ffma2_rn(G2, P13, __fmul2_rn(G3, P12)));
-        const float2 den = __ffma2_rn(make_float2(6.f, 6.f), P13, __ffma2_rn(make_float2(3.f, 3.f), P12, P23));
+        const float2 den = __ffma2_rn(kWenoPairs[7], P13, __ffma2_rn(kWenoPairs[8], P12, P23));
         const float2 r = make_float2(rcp_approx(den.x), rcp_approx(den.y));
         return __ffma2_rn(num, r, c);
     }
