@@ -99,3 +99,28 @@ def fit_density_law(res, dmax: float = 6.0):
     sel = [r for r in res if r["Drho"] < dmax]
     e, c = np.polyfit(np.log([r["Drho"] for r in sel]), [r["gamma"] for r in sel], 1)
     return float(c), float(e)
+
+
+def main(argv=None):
+    """python -m paper_1010_4124_gb300.sweeps {velocity,density,hybrid} [--steps N]
+    runs one of the paper's studies as a batch and prints the growth rates and
+    the fitted law."""
+    import argparse
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("study", choices=sorted(SWEEPS))
+    ap.add_argument("--steps", type=int, default=40000)
+    ap.add_argument("--sample-every", type=int, default=50)
+    args = ap.parse_args(argv)
+    res = run(args.study, steps=args.steps, sample_every=args.sample_every)
+    for r in res:
+        print(f"D_v = {r['Dv']:6.2f}  D_rho = {r['Drho']:6.2f}  R = {r['R']:5.2f}  gamma = {r['gamma']:.4f}")
+    if args.study == "velocity":
+        a, b = fit_velocity_law(res)
+        print(f"ln gamma_v = a - b D_v: a = {a:.4f}, b = {b:.5f}   (paper: a = 2.70, b = 0.07)")
+    elif args.study == "density":
+        c, e = fit_density_law(res)
+        print(f"gamma_rho = c + e ln D_rho (D_rho < 6): c = {c:.4f}, e = {e:.4f}   (paper: c = 5.28, e = 0.62)")
+
+
+if __name__ == "__main__":
+    main()
