@@ -222,12 +222,28 @@ __device__ __forceinline__ void top_faces(const StepConst<float>& c, const float
 struct TileInfo {
     int x0, y0, bxa;
 };
+// t / d and t % d for 0 <= t < 2^24 and d >= 1, without an integer division:
+// the quotient estimated from the correctly rounded reciprocal inv_d of d,
+// corrected by one step (exact over that range)
+__device__ __forceinline__ int2 tile_divmod(int t, int d, float inv_d) {
+    int q = __float2int_rz(__fmul_rn(__int2float_rn(t), inv_d));
+    int r = t - q * d;
+    if (r < 0) {
+        --q;
+        r += d;
+    } else if (r >= d) {
+        ++q;
+        r -= d;
+    }
+    return make_int2(q, r);
+}
 template <int TY>
-__device__ __forceinline__ TileInfo tile_info(int t, int tiles_x) {
+__device__ __forceinline__ TileInfo tile_info(int t, int tiles_x, float inv_tx) {
     TileInfo ti;
-    const int tx = t % tiles_x;
+    const int2 qr = tile_divmod(t, tiles_x, inv_tx);
+    const int tx = qr.y;
     ti.x0 = v3::TW * tx - GX;  // interior column of lane 0
-    ti.y0 = (t / tiles_x) * TY;
+    ti.y0 = qr.x * TY;
     ti.bxa = v3::TW * tx - 4;  // array column of the box start (16-byte aligned; -4 reads zeros)
     return ti;
 }
@@ -272,7 +288,7 @@ __global__ void __launch_bounds__(32 * TY, 16 / TY) step_f32_kernel(const __grid
     for (int i = tid; i < ninst; i += blockDim.x) first[i] = descs[i].first_tile;
     auto issue = [&](int t, int b) {
         const InstDesc* D = descs + find_inst(first, ninst, t);
-        const TileInfo ti = tile_info<TY>(t - D->first_tile, D->tiles_x);
+        const TileInfo ti = tile_info<TY>(t - D->first_tile, D->tiles_x, __frcp_rn((float)D->tiles_x));
         const uint32_t bar = smem_u32(&full[b]);
         tensormap_acquire(&D->map);
         mbar_arrive_expect_tx(bar, (uint32_t)(sizeof(float) * S::BOX_FLOATS));
@@ -294,6 +310,7 @@ __global__ void __launch_bounds__(32 * TY, 16 / TY) step_f32_kernel(const __grid
     // fields of the instance of the current tile, read from global memory
     // only when the instance changes (tiles of one instance are contiguous)
     int cur = -1, first_t = 0, tiles_x = 1;
+    float inv_tx = 1.f;
     Geom g{};
     float* out = nullptr;
     int k = 0;  // local tile counter: buffer k & 1, phase (k >> 1) & 1
@@ -318,10 +335,11 @@ __global__ void __launch_bounds__(32 * TY, 16 / TY) step_f32_kernel(const __grid
             out = D->out;
             first_t = D->first_tile;
             tiles_x = D->tiles_x;
+            inv_tx = __frcp_rn((float)tiles_x);
             cur = inst;
         }
         const float* tile = buf + b * S::BUF_FLOATS;
-        const TileInfo ti = tile_info<TY>(t - first_t, tiles_x);
+        const TileInfo ti = tile_info<TY>(t - first_t, tiles_x, inv_tx);
         const int ix = ti.x0 + lane, iy = ti.y0 + ty;
         const int s = lane + 4;  // smem column of the node
         const int r = ty + 3;    // smem row of the node
@@ -397,9 +415,10 @@ __device__ __forceinline__ void diag_cta(const StepConst<float>& c, const Geom& 
                                          const float* __restrict__ f, double* __restrict__ partial, int cta,
                                          int ncta) {
     const int tid = threadIdx.x, ty = tid >> 5, lane = tid & 31;
+    const float inv_tx = __frcp_rn((float)tiles_x);
     // the node of tile t for this thread, its activity and its 19 values
     auto load = [&](int t, float fl[NQ]) {
-        const TileInfo ti = tile_info<TY>(t, tiles_x);
+        const TileInfo ti = tile_info<TY>(t, tiles_x, inv_tx);
         const int ix = ti.x0 + lane, iy = ti.y0 + ty;
         const bool active = ix >= 0 && ix < g.nx && iy < g.ny;
 #pragma unroll
