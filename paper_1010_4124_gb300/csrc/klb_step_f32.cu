@@ -47,8 +47,10 @@ void f32_box(int variant, unsigned* bx, unsigned* by, unsigned* bz) {
 
 cudaError_t prepare_f32_kernels() {
     num_sms();
-    cudaError_t e = set_attr_f32<8, 0>();
-    return e != cudaSuccess ? e : set_attr_f32<16, 0>();
+    cudaError_t e = set_attr_f32<8, 0, false>();
+    if (e == cudaSuccess) e = set_attr_f32<16, 0, false>();
+    if (e == cudaSuccess) e = set_attr_f32<8, 0, true>();
+    return e != cudaSuccess ? e : set_attr_f32<16, 0, true>();
 }
 
 cudaError_t launch_step_f32(const StepConst<float>& c, const InstDesc* descs, int ninst, int ntiles,
@@ -61,9 +63,16 @@ cudaError_t launch_step_f32(const StepConst<float>& c, const InstDesc* descs, in
     if (c.scheme != 0)
         return launch_step_f32_lo(c, descs, ninst, ntiles, diag_partials, err, spin_limit, inject,
                                   rows_of(variant), grid, stream);
+    const bool multi = ninst > 1;
     if (rows_of(variant) == 8)
-        return launch_f32_t<8, 0>(c, descs, ninst, ntiles, diag_partials, err, spin_limit, inject, grid, stream);
-    return launch_f32_t<16, 0>(c, descs, ninst, ntiles, diag_partials, err, spin_limit, inject, grid, stream);
+        return multi ? launch_f32_t<8, 0, true>(c, descs, ninst, ntiles, diag_partials, err, spin_limit, inject, grid,
+                                                stream)
+                     : launch_f32_t<8, 0, false>(c, descs, ninst, ntiles, diag_partials, err, spin_limit, inject,
+                                                 grid, stream);
+    return multi ? launch_f32_t<16, 0, true>(c, descs, ninst, ntiles, diag_partials, err, spin_limit, inject, grid,
+                                             stream)
+                 : launch_f32_t<16, 0, false>(c, descs, ninst, ntiles, diag_partials, err, spin_limit, inject, grid,
+                                              stream);
 }
 
 cudaError_t launch_diag_f32_batch(const StepConst<float>& c, const DiagJob* jobs, int njobs, int total_ctas,

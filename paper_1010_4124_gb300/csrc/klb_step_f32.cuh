@@ -267,7 +267,9 @@ __device__ __forceinline__ void tensormap_acquire(const void* map) {
     asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
 }
 
-template <int TY, int SCH>
+// MULTI: the launch may cover several grids (a batch); a single grid
+// (MULTI false) skips the instance lookup altogether.
+template <int TY, int SCH, bool MULTI>
 __global__ void __launch_bounds__(32 * TY, 16 / TY) step_f32_kernel(const __grid_constant__ StepConst<float> c,
                                                                     const InstDesc* __restrict__ descs, int ninst,
                                                                     int ntiles, double* __restrict__ diag_partials,
@@ -282,12 +284,17 @@ __global__ void __launch_bounds__(32 * TY, 16 / TY) step_f32_kernel(const __grid
     __shared__ __align__(8) uint64_t full[2];
     __shared__ __align__(8) uint64_t never;  // fault injection: a barrier nothing arrives on
     __shared__ int first[kMaxInstances];
+    // the instance of the tile in each buffer, written by the thread that
+    // issues the copy and read by all after the next CTA barrier
+    __shared__ int tile_inst[2];
     __shared__ float edges[TY][v3::NXV];
 
     const int tid = threadIdx.x, ty = tid >> 5, lane = tid & 31;
     for (int i = tid; i < ninst; i += blockDim.x) first[i] = descs[i].first_tile;
     auto issue = [&](int t, int b) {
-        const InstDesc* D = descs + find_inst(first, ninst, t);
+        const int inst = MULTI ? find_inst(first, ninst, t) : 0;
+        if (MULTI) tile_inst[b] = inst;
+        const InstDesc* D = descs + inst;
         const TileInfo ti = tile_info<TY>(t - D->first_tile, D->tiles_x, __frcp_rn((float)D->tiles_x));
         const uint32_t bar = smem_u32(&full[b]);
         tensormap_acquire(&D->map);
@@ -328,7 +335,7 @@ __global__ void __launch_bounds__(32 * TY, 16 / TY) step_f32_kernel(const __grid
         bool late = !mbar_wait_bounded(smem_u32(&full[b]), (k >> 1) & 1, spin_limit);
         if (inject) late = late || !mbar_wait_bounded(smem_u32(&never), 0, spin_limit);
         float* yf = yf0 + (S::YB == 2 ? b : 0) * S::YF_FLOATS;
-        const int inst = find_inst(first, ninst, t);
+        const int inst = MULTI ? tile_inst[b] : 0;
         if (inst != cur) {
             const InstDesc* D = descs + inst;
             g = D->g;
@@ -467,11 +474,11 @@ __global__ void __launch_bounds__(32 * TY) diag_f32_batch_kernel(const StepConst
 }
 
 // dynamic shared memory of the kernel instance, set once per process
-template <int TY, int SCH>
+template <int TY, int SCH, bool MULTI>
 cudaError_t set_attr_f32() {
     static bool done = false;
     if (!done) {
-        cudaError_t e = cudaFuncSetAttribute(step_f32_kernel<TY, SCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(step_f32_kernel<TY, SCH, MULTI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)v3::Shape<TY>::SMEM_BYTES);
         if (e != cudaSuccess) return e;
         done = true;
@@ -479,13 +486,13 @@ cudaError_t set_attr_f32() {
     return cudaSuccess;
 }
 
-template <int TY, int SCH>
+template <int TY, int SCH, bool MULTI>
 cudaError_t launch_f32_t(const StepConst<float>& c, const InstDesc* descs, int ninst, int ntiles,
                          double* diag_partials, int* err, long long spin_limit, int inject, int grid,
                          cudaStream_t stream) {
-    cudaError_t e = set_attr_f32<TY, SCH>();
+    cudaError_t e = set_attr_f32<TY, SCH, MULTI>();
     if (e != cudaSuccess) return e;
-    step_f32_kernel<TY, SCH><<<grid, 32 * TY, v3::Shape<TY>::SMEM_BYTES, stream>>>(c, descs, ninst, ntiles,
+    step_f32_kernel<TY, SCH, MULTI><<<grid, 32 * TY, v3::Shape<TY>::SMEM_BYTES, stream>>>(c, descs, ninst, ntiles,
                                                                                  diag_partials, err, spin_limit,
                                                                                  inject);
     return cudaGetLastError();
