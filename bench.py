@@ -339,7 +339,8 @@ def sweep_measure(steps: int, torch):
     seed, FP32, diagnostics every 10 steps): one persistent launch per step
     over all instances, replayed from a CUDA graph, tiles picked by the
     autotuner -- against looping the plain single-grid step (same tile shape)
-    over the 32 instances one after another on the same GPU."""
+    over the 32 instances one after another on the same GPU, and against the
+    batch with the other tile shape."""
     import numpy as np
     from paper_1010_4124_gb300 import inputs, klb
     pbs = inputs.sweep_instances(steps)
@@ -362,6 +363,20 @@ def sweep_measure(steps: int, torch):
         t_batch = e0.elapsed_time(e1) * 1e-3
         launches = bt.launch_count - n0
         tiles = bt.tiles
+        # the other tile shape, timed the same way from the initial state:
+        # evidence for the pick
+        other = 1 - variant
+        bt.variant = other
+        for m, fl in zip(bt.members, fields):
+            m.init_fields(*fl)
+        bt.step(70)
+        bt.sync()
+        e0.record(stream)
+        bt.step(steps)
+        e1.record(stream)
+        e1.synchronize()
+        bt.sync()
+        t_other = e0.elapsed_time(e1) * 1e-3
     # the plain step, looped over the instances, with the batch's tile shape
     hs = []
     for pb, fl in zip(pbs, fields):
@@ -385,6 +400,7 @@ def sweep_measure(steps: int, torch):
             "batched_gcell_s": round(cells * steps / t_batch / 1e9, 4),
             "looped_plain_gcell_s": round(cells * steps / t_loop / 1e9, 4),
             "speedup_vs_looped_plain": round(t_loop / t_batch, 3),
+            "other_tiles": {"kernel_variant": other, "batched_gcell_s": round(cells * steps / t_other / 1e9, 4)},
             "sizes": sorted({f"{pb.nx}x{pb.ny}" for pb in pbs})}
 
 
