@@ -7,6 +7,7 @@
 // every instance is a full grid with its own fields, boundaries and
 // diagnostics series; the instances share the step constants (dx, dy, dt,
 // tau, ring speeds, epsilon).
+#include <limits.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -69,6 +70,9 @@ static int upload(klb_batch_t* b) {
         klb_t* h = b->m[i];
         int tiles_x, nt;
         f32_tiles(h->g.nx, h->g.ny, b->variant, &tiles_x, &nt);
+        // per member below 2^24 tiles (the float quotient estimate of the tile
+        // map is exact there), and the batch's tile index space within int
+        if (nt >= (1 << 24) || first > INT_MAX - nt) return bfail(b, KLB_E_INVAL, "batch too large for the FP32 tile index");
         for (int p = 0; p < 2; ++p) {
             InstDesc& e = d[(size_t)p * n + i];
             memset(&e, 0, sizeof(InstDesc));

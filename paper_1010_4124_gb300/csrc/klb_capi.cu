@@ -449,6 +449,9 @@ int fdlb::handle_upload_descs(klb_t* h) {
     if (h->p.precision != KLB_FP32) return KLB_OK;
     int tiles_x, ntiles;
     f32_tiles(h->g.nx, h->g.ny, h->variant, &tiles_x, &ntiles);
+    // the kernels split a tile index into (row, column) by a float quotient
+    // estimate that is exact below 2^24 tiles
+    if (ntiles >= (1 << 24)) return fail(h, KLB_E_INVAL, "grid too large for the FP32 tile index (2^24 tiles)");
     InstDesc d[2];
     for (int p = 0; p < 2; ++p) {  // descriptor p: the state is in buf[p], the next one goes to buf[1 - p]
         memset(&d[p], 0, sizeof(InstDesc));
