@@ -91,7 +91,8 @@ void klb_params_default(klb_params* p);
  * return a handle in *out.  Ownership: the caller destroys it with
  * klb_destroy.  Logs (stderr) a warning when dt/tau > 2 or the convective CFL
  * number max(v) dt / min(dx, dy) > 0.03 (forward Euler with WENO5 then grows
- * linearly unstable modes).  Errors: KLB_E_INVAL, KLB_E_NOMEM, KLB_E_CUDA. */
+ * linearly unstable modes).  Errors: KLB_E_INVAL (also for an FP32 grid of
+ * 2^24 tiles or more, about 2^32 nodes), KLB_E_NOMEM, KLB_E_CUDA. */
 int klb_create(const klb_params* p, klb_t** out);
 
 /* Free every resource of the handle.  NULL-safe. */
@@ -184,7 +185,7 @@ int64_t klb_launch_count(const klb_t* h);
  * handle starts with the shape measured faster for its size: 1 up to 40
  * sixteen-row tiles per SM (about 2048 x 1024 nodes on 152 SMs), 0 beyond.
  * The FP64 step has variant 0 only.  Synchronises the handle's stream.
- * Errors: KLB_E_INVAL. */
+ * Errors: KLB_E_INVAL (the handle then keeps its tile shape), KLB_E_CUDA. */
 int klb_set_variant(klb_t* h, int variant);
 int klb_get_variant(const klb_t* h);
 

@@ -626,7 +626,15 @@ int klb_set_variant(klb_t* h, int variant) {
             return r;
         }
     }
-    return fdlb::handle_upload_descs(h);
+    int r = fdlb::handle_upload_descs(h);
+    if (r != KLB_OK) {  // keep the handle as it was (maps and descriptors of the old tile shape)
+        const std::string msg = h->err;
+        h->variant = old;
+        for (int j = 0; j < 2; ++j) make_map(h, h->buf[j], &h->map[j]);
+        fdlb::handle_upload_descs(h);
+        h->err = msg;
+    }
+    return r;
 }
 
 int klb_get_variant(const klb_t* h) { return h ? h->variant : -1; }
