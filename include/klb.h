@@ -185,7 +185,10 @@ int64_t klb_launch_count(const klb_t* h);
  * handle starts with the shape measured faster for its size: 1 up to 40
  * sixteen-row tiles per SM (about 2048 x 1024 nodes on 152 SMs), 0 beyond.
  * The FP64 step has variant 0 only.  Synchronises the handle's stream.
- * Errors: KLB_E_INVAL (the handle then keeps its tile shape), KLB_E_CUDA. */
+ * Errors: KLB_E_INVAL or KLB_E_CUDA, after which the handle keeps its tile
+ * shape; KLB_E_STATE when putting the old shape back failed as well: the
+ * handle then refuses klb_step (and batches holding it refuse to step) and
+ * should be destroyed. */
 int klb_set_variant(klb_t* h, int variant);
 int klb_get_variant(const klb_t* h);
 

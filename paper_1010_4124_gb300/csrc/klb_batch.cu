@@ -119,6 +119,7 @@ static int upload(klb_batch_t* b) {
 static int same_state(klb_batch_t* b) {
     for (klb_t* h : b->m) {
         if (!h->initialized) return bfail(b, KLB_E_STATE, "a member has no initial state (klb_init_fields)");
+        if (h->broken) return bfail(b, KLB_E_STATE, "a member's tile shape could not be restored (klb_set_variant)");
         if (h->cur != b->m[0]->cur || h->steps != b->m[0]->steps)
             return bfail(b, KLB_E_STATE, "members are not at the same step (re-initialise them together)");
     }

@@ -503,6 +503,7 @@ int klb_step(klb_t* h, int64_t n) {
     if (!h) return KLB_E_INVAL;
     if (n < 0) return fail(h, KLB_E_INVAL, "negative step count");
     if (!h->initialized) return fail(h, KLB_E_STATE, "klb_step before klb_init_fields");
+    if (h->broken) return fail(h, KLB_E_STATE, "the handle's tile shape could not be restored (klb_set_variant)");
     for (int64_t s = 0; s < n; ++s) {
         int r = one_step(h);
         if (r != KLB_OK) return r;
@@ -616,25 +617,30 @@ int klb_set_variant(klb_t* h, int variant) {
     }
     CK(h, cudaStreamSynchronize(h->stream));
     const int old = h->variant;
+    // put the old tile shape back (maps and descriptors); a rollback that
+    // fails leaves the handle unusable rather than silently inconsistent
+    auto rollback = [&](int code) {
+        const std::string msg = h->err;
+        h->variant = old;
+        bool ok = true;
+        for (int j = 0; j < 2; ++j) ok = make_map(h, h->buf[j], &h->map[j]) == KLB_OK && ok;
+        ok = ok && fdlb::handle_upload_descs(h) == KLB_OK;
+        if (!ok) {
+            h->broken = true;
+            return fail(h, KLB_E_STATE, msg + "; restoring the previous tile shape failed too (" + h->err +
+                                            "): the handle refuses further steps");
+        }
+        h->err = msg;
+        return code;
+    };
     h->variant = variant;
     for (int i = 0; i < 2; ++i) {
         int r = make_map(h, h->buf[i], &h->map[i]);
-        if (r != KLB_OK) {
-            h->variant = old;
-            for (int j = 0; j < 2; ++j) make_map(h, h->buf[j], &h->map[j]);
-            fdlb::handle_upload_descs(h);
-            return r;
-        }
+        if (r != KLB_OK) return rollback(r);
     }
     int r = fdlb::handle_upload_descs(h);
-    if (r != KLB_OK) {  // keep the handle as it was (maps and descriptors of the old tile shape)
-        const std::string msg = h->err;
-        h->variant = old;
-        for (int j = 0; j < 2; ++j) make_map(h, h->buf[j], &h->map[j]);
-        fdlb::handle_upload_descs(h);
-        h->err = msg;
-    }
-    return r;
+    if (r != KLB_OK) return rollback(r);  // keep the handle as it was
+    return KLB_OK;
 }
 
 int klb_get_variant(const klb_t* h) { return h ? h->variant : -1; }

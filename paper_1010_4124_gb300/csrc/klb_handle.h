@@ -33,6 +33,7 @@ struct klb {  // state of one grid
     int64_t steps = 0;
     bool pending_sample = false;
     bool initialized = false;
+    bool broken = false;          // a failed tile-shape rollback left maps and descriptors inconsistent
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int64_t launches = 0;

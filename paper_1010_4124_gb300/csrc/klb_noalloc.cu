@@ -11,6 +11,7 @@
 // cannot afford the device-wide synchronisation of cudaMalloc/cudaFree.
 // The first call on each device looks up the scratch's device address; make
 // it before any stream capture.
+#include <climits>
 #include <mutex>
 
 #include "klb_handle.h"
@@ -83,6 +84,22 @@ int klb_diagnostics_static(const void* f, int32_t precision, int32_t nx, int32_t
     if (nx < 1 || ny < 1 || pitch < nx + GX + 3 || plane < pitch * (int64_t)(ny + 2 * GY)) {
         g_static_error = "inconsistent grid size, pitch or plane stride";
         return KLB_E_INVAL;
+    }
+    // the kernels keep the row pitch and the row index (ghost rows included)
+    // in int and form element offsets in 64 bits
+    if (pitch > INT_MAX || (int64_t)ny + 2 * GY > INT_MAX) {
+        g_static_error = "row pitch beyond the int range of the kernels' row arithmetic";
+        return KLB_E_INVAL;
+    }
+    if (precision == KLB_FP32) {
+        // the FP32 reduction splits a tile index into (row, column) by a float
+        // quotient estimate that is exact below 2^24 tiles
+        int tiles_x = 0, ntiles = 0;
+        f32_tiles(nx, ny, 0, &tiles_x, &ntiles);
+        if (ntiles >= (1 << 24)) {
+            g_static_error = "grid too large for the FP32 tile index (2^24 tiles)";
+            return KLB_E_INVAL;
+        }
     }
     // partial records the reduction writes, against the scratch capacity
     const long long records =
