@@ -75,7 +75,11 @@ typedef struct {
     int32_t precision;        /* klb_prec: storage and arithmetic type of f on the device */
     int32_t sample_every;     /* diagnostics every n steps (0 = off); see klb_diagnostics */
     int32_t diag_capacity;    /* samples kept on the device (0 = 4096); older samples are dropped */
-    double eps;               /* WENO epsilon of Eq. 52; 0 selects the paper's 1e-6 */
+    double eps;               /* WENO epsilon of Eq. 52; 0 selects the paper's 1e-6.  FP32
+                               * WENO5 needs 3/4 eps / max(v)^2 >= 2e-19 (the squared
+                               * smoothness indicators stay normal FP32 numbers) and keeps
+                               * its weights exact while the smallest indicator of a face
+                               * is below 9e18 (differences of f up to about 1e9) */
     void* stream;             /* cudaStream_t to enqueue on; NULL = a stream owned by the handle */
     int32_t scheme;           /* klb_scheme: convection scheme of the x and y fluxes (default WENO5) */
 } klb_params;
@@ -92,7 +96,8 @@ void klb_params_default(klb_params* p);
  * klb_destroy.  Logs (stderr) a warning when dt/tau > 2 or the convective CFL
  * number max(v) dt / min(dx, dy) > 0.03 (forward Euler with WENO5 then grows
  * linearly unstable modes).  Errors: KLB_E_INVAL (also for an FP32 grid of
- * 2^24 tiles or more, about 2^32 nodes), KLB_E_NOMEM, KLB_E_CUDA. */
+ * 2^24 tiles or more, about 2^32 nodes, and for an FP32 WENO5 eps below the
+ * range given at klb_params.eps), KLB_E_NOMEM, KLB_E_CUDA. */
 int klb_create(const klb_params* p, klb_t** out);
 
 /* Free every resource of the handle.  NULL-safe. */

@@ -173,10 +173,9 @@ struct ArithF32 {
         const T O = __fmul_rn(w, fmaf(w2, 1.f / 6.f, s.A));
         return __fmul_rn(s.rF[k + 1], i < 3 ? __fadd_rn(E, O) : __fsub_rn(E, O));
     }
-    // WENO5 flux on the unscaled plane (eps already divided by v^2), over a
-    // common denominator: h = c + sum delta_q g_q P_q / sum delta_q P_q with
-    // g_q = h_q - c (Eqs. 49-51) and P_q the product of the other two
-    // (eps + sigma)^2 (Eqs. 52-55); one reciprocal instead of four divisions.
+    // WENO5 flux on the unscaled plane (eps already divided by v^2): with the
+    // weights alpha_q = delta_q / (eps + sigma_q)^2 of Eq. (52) and the
+    // candidates h_q of Eqs. (49)-(51), h = c + sum alpha_q (h_q - c) / sum alpha_q.
     // Since every term scales with v except the absolute epsilon,
     // h(v f; eps) = v h(f; eps / v^2): the factor v sits in the update.
     __device__ __forceinline__ static T weno(T a, T b, T c, T d, T e, T eps) {
@@ -187,16 +186,20 @@ struct ArithF32 {
         //   s_2 = D2 (D2 - 5/4 D3) + D3^2,
         //   s_3 = e4 (e4 + 11/4 D3) + 5/2 D3^2,
         // and eps (the constant passed in) is scaled by 3/4 as well: the
-        // common factor cancels in the weights.  The candidates of Eqs. (49)-(51)
-        // relative to c read h_1 - c = (5 D2 + 2 D1)/6, h_2 - c = (D2 + 2 D3)/6,
-        // h_3 - c = (4 D3 + e4)/6; with the optimal weights delta_q and the 1/6
-        // folded in, and numerator and denominator both scaled by 10 (their
-        // ratio is unchanged),
-        //   h = c + (G1 P23 + G2 P13 + G3 P12) / (P23 + 6 P13 + 3 P12),
+        // common factor cancels in the weights.  The candidates relative to c
+        // read h_1 - c = (5 D2 + 2 D1)/6, h_2 - c = (D2 + 2 D3)/6,
+        // h_3 - c = (4 D3 + e4)/6; with the optimal weights delta_q and the
+        // 1/6 folded in, and numerator and denominator both scaled by 10,
+        //   h = c + (G1 w1 + G2 w2 + G3 w3) / (w1 + 6 w2 + 3 w3),
         //   G1 = 5/6 D2 + 1/3 D1, G2 = D2 + 2 D3, G3 = 2 D3 + e4 / 2,
-        // with P the products of the other two (eps + sigma)^2.  The sign of D1
-        // and the common factor 10 let the packed form use few distinct
-        // constant pairs (each costs a register pair or a reload).
+        // with w_q = 1 / s_q^2 (one reciprocal each, and one of the sum).
+        // Range: s_q^2 stays a normal FP32 number for 1.1e-19 <= s_q <= 1.8e19;
+        // s_q >= eps always, so eps (3/4 eps / v^2 of the finest velocity
+        // component) must be at least 1.1e-19, and the weights stay exact
+        // while the smallest indicator of a face is below 9e18 (differences
+        // of f up to about 1e9).  (A common denominator of products of the
+        // squared indicators, one reciprocal per face, spans s^4: it fails
+        // below eps ~ 2e-10 and above differences ~ 3e4.)
         // Every operation is an explicitly rounded multiply, add or fused
         // multiply-add, in the same order as each lane of weno2(), so the
         // scalar and packed evaluations give the same bits.
@@ -205,19 +208,19 @@ struct ArithF32 {
         const T s1 = fmaf(d1, fmaf(2.75f, d2, d1), fmaf(2.5f, a2, eps));
         const T s2 = fmaf(d2, fmaf(-1.25f, d3, d2), fmaf(d3, d3, eps));
         const T s3 = fmaf(e4, fmaf(2.75f, d3, e4), fmaf(2.5f, a3, eps));
-        const T p1 = __fmul_rn(s1, s1), p2 = __fmul_rn(s2, s2), p3 = __fmul_rn(s3, s3);
-        const T P23 = __fmul_rn(p2, p3), P13 = __fmul_rn(p1, p3), P12 = __fmul_rn(p1, p2);
+        const T w1 = rcp_approx(__fmul_rn(s1, s1)), w2 = rcp_approx(__fmul_rn(s2, s2));
+        const T w3 = rcp_approx(__fmul_rn(s3, s3));
         const T G1 = fmaf(5.f / 6.f, d2, __fmul_rn(1.f / 3.f, d1));
         const T t3 = __fadd_rn(d3, d3);  // 2 D3, shared by G2 and G3
         const T G2 = __fadd_rn(d2, t3);
         const T G3 = fmaf(0.5f, e4, t3);
-        const T num = fmaf(G1, P23, fmaf(G2, P13, __fmul_rn(G3, P12)));
-        const T den = fmaf(6.f, P13, fmaf(3.f, P12, P23));
+        const T num = fmaf(G1, w1, fmaf(G2, w2, __fmul_rn(G3, w3)));
+        const T den = fmaf(6.f, w2, fmaf(3.f, w3, w1));
         return fmaf(num, rcp_approx(den), c);
     }
     // The same flux for two independent faces at once (packed f32x2
-    // arithmetic: one instruction for both lanes of the pair).  Its constant
-    // pairs come from constant memory (kWenoPairs).
+    // arithmetic: one instruction for both lanes of the pair; the reciprocals
+    // are per lane).  Its constant pairs come from constant memory (kWenoPairs).
     __device__ __forceinline__ static float2 weno2(float2 a, float2 b, float2 c, float2 d, float2 e, float2 eps) {
         // lane by lane the same operations as weno()
         const float2 m1 = kWenoPairs[0];
@@ -229,13 +232,15 @@ struct ArithF32 {
         const float2 s2 = __ffma2_rn(d2, __ffma2_rn(kWenoPairs[3], d3, d2), __ffma2_rn(d3, d3, eps));
         const float2 s3 = __ffma2_rn(e4, __ffma2_rn(k275, d3, e4), __ffma2_rn(k25, a3, eps));
         const float2 p1 = __fmul2_rn(s1, s1), p2 = __fmul2_rn(s2, s2), p3 = __fmul2_rn(s3, s3);
-        const float2 P23 = __fmul2_rn(p2, p3), P13 = __fmul2_rn(p1, p3), P12 = __fmul2_rn(p1, p2);
+        const float2 w1 = make_float2(rcp_approx(p1.x), rcp_approx(p1.y));
+        const float2 w2 = make_float2(rcp_approx(p2.x), rcp_approx(p2.y));
+        const float2 w3 = make_float2(rcp_approx(p3.x), rcp_approx(p3.y));
         const float2 G1 = __ffma2_rn(kWenoPairs[4], d2, __fmul2_rn(kWenoPairs[5], d1));
         const float2 t3 = __fadd2_rn(d3, d3);
         const float2 G2 = __fadd2_rn(d2, t3);
         const float2 G3 = __ffma2_rn(kWenoPairs[6], e4, t3);
-        const float2 num = __ffma2_rn(G1, P23, __ffma2_rn(G2, P13, __fmul2_rn(G3, P12)));
-        const float2 den = __ffma2_rn(kWenoPairs[7], P13, __ffma2_rn(kWenoPairs[8], P12, P23));
+        const float2 num = __ffma2_rn(G1, w1, __ffma2_rn(G2, w2, __fmul2_rn(G3, w3)));
+        const float2 den = __ffma2_rn(kWenoPairs[7], w2, __ffma2_rn(kWenoPairs[8], w3, w1));
         const float2 r = make_float2(rcp_approx(den.x), rcp_approx(den.y));
         return __ffma2_rn(num, r, c);
     }

@@ -207,3 +207,16 @@ def rough_random_fields(nx: int, ny: int, seed: int):
     uy = rng.uniform(-0.2, 0.2, size=(ny, nx))
     T = rng.uniform(0.6, 1.2, size=(ny, nx))
     return rho, ux, uy, T
+
+
+def blocky_fields(nx: int, ny: int, seed: int, block: int = 8):
+    """Piecewise-constant state: uniform blocks of block x block nodes with
+    seeded random (rho, ux, uy, T) each, so that most stencils see uniform
+    data (smoothness indicators equal to epsilon) and the rest a jump."""
+    rng = np.random.default_rng(seed)
+    by, bx = (ny + block - 1) // block, (nx + block - 1) // block
+    out = []
+    for lo, hi in ((0.5, 1.5), (-0.2, 0.2), (-0.2, 0.2), (0.6, 1.2)):
+        g = rng.uniform(lo, hi, size=(by, bx))
+        out.append(np.repeat(np.repeat(g, block, axis=0), block, axis=1)[:ny, :nx].copy())
+    return tuple(out)

@@ -129,3 +129,14 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
         klb.lib()
     with pytest.raises(RuntimeError):
         klb.Klb(klb.make_params(8, 8, 0.01, 0.01, 1e-5, 1e-5))
+
+
+def test_fp32_weno_eps_below_the_range_is_refused(lib):
+    # klb_create validates before touching the device: an FP32 WENO5 handle
+    # whose 3/4 eps / max(v)^2 is below 2e-19 (squared smoothness indicators
+    # below the normal FP32 range) is refused with KLB_E_INVAL
+    from paper_1010_4124_gb300 import klb
+    p = klb.make_params(32, 32, 0.002, 0.002, 1e-5, 1e-5, precision="fp32", eps=1e-18)
+    h = C.c_void_p()
+    assert klb.lib().klb_create(C.byref(p), C.byref(h)) == -1
+    assert b"eps" in klb.lib().klb_last_error(None)

@@ -1,0 +1,70 @@
+"""FP32 step over the range of the method's inputs, against the FP64 oracle.
+
+The FP32 WENO5 weights square the smoothness indicators (Eq. 52); these tests
+run the FP32 kernels (both tile shapes) on states whose indicators span many
+orders of magnitude and hold them to the FP32 bar of the oracle (1e-5 of the
+scale of f, and of rho, u, T):
+  * smooth, rough (random node-to-node jumps), piecewise-constant (uniform
+    blocks: indicators equal to epsilon, next to jumps) and KHI states;
+  * the density scaled by 1e-3, 1e3 and 1e4 (f scales with it; epsilon is
+    absolute, so the weights see other ratios of indicator to epsilon);
+  * epsilon 1e-6 (the paper's) and 1e-10.
+One step from each state (both tile shapes, bit for bit equal) and 100 steps.
+"""
+import numpy as np
+import pytest
+
+from gpu_common import gpu_handle, oracle_params, rel_err_fields, rel_err_global
+from oracle import core
+from paper_1010_4124_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+NX, NY = 70, 45  # three tile columns (ragged), several tile rows of either shape
+
+
+def _state(kind, scale):
+    if kind == "khi":
+        pb = inputs.khi(NX, NY, 100, Dv=3.0, Drho=3.0, sample_every=0)
+        rho, ux, uy, T = inputs.fields(pb)
+    else:
+        pb = inputs.Problem(kind, NX, NY, 0.002, 0.002, 1e-5, 1e-5, 100,
+                            bc_x=("periodic", "periodic"), bc_y=("outflow", "outflow"))
+        gen = {"smooth": lambda: inputs.smooth_random_fields(NX, NY, seed=21, amp=0.08),
+               "rough": lambda: inputs.rough_random_fields(NX, NY, seed=22),
+               "blocky": lambda: inputs.blocky_fields(NX, NY, seed=23, block=8)}[kind]
+        rho, ux, uy, T = gen()
+    return pb, [np.ascontiguousarray(a) for a in (scale * rho, ux, uy, T)]
+
+
+def _check(got, ref, p, tol, what):
+    assert np.all(np.isfinite(got)), what
+    e = rel_err_global(got, ref)
+    errs = rel_err_fields(got, ref, p)
+    assert e <= tol and max(errs["rho"], errs["u"], errs["T"]) <= tol, (what, e, errs)
+    return e, errs
+
+
+@pytest.mark.parametrize("eps", [1e-6, 1e-10])
+@pytest.mark.parametrize("scale", [1e-3, 1.0, 1e3, 1e4])
+@pytest.mark.parametrize("kind", ["smooth", "rough", "blocky", "khi"])
+def test_fp32_over_the_range(kind, scale, eps):
+    pb, fields = _state(kind, scale)
+    p = oracle_params(pb, eps=eps)
+    f0 = core.init_feq(p, *fields)
+    ref1 = core.step(p, f0)
+    ref100, _ = core.run(p, f0, 100)
+    one, hundred = [], None
+    for v in (0, 1):
+        with gpu_handle(pb, "fp32", eps=eps) as h:
+            h.variant = v
+            h.init_fields(*fields)
+            h.step(1)
+            one.append(h.get_f())
+            if v == 0:
+                h.step(99)
+                hundred = h.get_f()
+    assert np.array_equal(one[0], one[1])
+    e1, _ = _check(one[0], ref1, p, 2e-6, (kind, scale, eps, 1))
+    e100, errs = _check(hundred, ref100, p, 1e-5, (kind, scale, eps, 100))
+    print(f"{kind} rho x {scale:g} eps {eps:g}: 1 step {e1:.2e}, 100 steps {e100:.2e} {errs}")
