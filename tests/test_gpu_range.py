@@ -3,7 +3,7 @@
 The FP32 WENO5 weights square the smoothness indicators (Eq. 52); these tests
 run the FP32 kernels (both tile shapes) on states whose indicators span many
 orders of magnitude and hold them to the FP32 bar of the oracle (1e-5 of the
-scale of f, and of rho, u, T):
+scale of f, and of rho, u, T; 2e-6 on rho, u, T after one step):
   * smooth, rough (random node-to-node jumps), piecewise-constant (uniform
     blocks: indicators equal to epsilon, next to jumps) and KHI states;
   * the density scaled by 1e-3, 1e3 and 1e4 (f scales with it; epsilon is
@@ -37,11 +37,11 @@ def _state(kind, scale):
     return pb, [np.ascontiguousarray(a) for a in (scale * rho, ux, uy, T)]
 
 
-def _check(got, ref, p, tol, what):
+def _check(got, ref, p, tol_f, tol_fields, what):
     assert np.all(np.isfinite(got)), what
     e = rel_err_global(got, ref)
     errs = rel_err_fields(got, ref, p)
-    assert e <= tol and max(errs["rho"], errs["u"], errs["T"]) <= tol, (what, e, errs)
+    assert e <= tol_f and max(errs["rho"], errs["u"], errs["T"]) <= tol_fields, (what, e, errs)
     return e, errs
 
 
@@ -65,6 +65,9 @@ def test_fp32_over_the_range(kind, scale, eps):
                 h.step(99)
                 hundred = h.get_f()
     assert np.array_equal(one[0], one[1])
-    e1, _ = _check(one[0], ref1, p, 2e-6, (kind, scale, eps, 1))
-    e100, errs = _check(hundred, ref100, p, 1e-5, (kind, scale, eps, 100))
+    # the FP32 bar (1e-5) on the scale of f and on rho, u, T; after one step
+    # the fields within 2e-6 (the FP32 rounding of f^(0), whose F_0 = 1 - 6 sum F_k
+    # cancels, puts ~2e-6 of the scale of f on the rest plane in one step)
+    e1, _ = _check(one[0], ref1, p, 1e-5, 2e-6, (kind, scale, eps, 1))
+    e100, errs = _check(hundred, ref100, p, 1e-5, 1e-5, (kind, scale, eps, 100))
     print(f"{kind} rho x {scale:g} eps {eps:g}: 1 step {e1:.2e}, 100 steps {e100:.2e} {errs}")
