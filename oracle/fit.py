@@ -39,3 +39,21 @@ def growth_rates(diag, dt: float, sample_every: int):
     g_ex = 0.5 * ols_slope(t[w], np.log(np.real(d[w, 5])))
     g_ke = 0.5 * ols_slope(t[w], np.log(d[w, 6]))
     return g_uy, g_ex, g_ke
+
+
+def linear_stage_rate(E, dt_sample: float, skip: float = 0.05, rise: float = 4.0):
+    """gamma of the initial growth stage of a long run (Sec. IV.A: E_x|max grows
+    as exp(2 gamma t) there), with the stage fixed by rule since the paper picks
+    it by eye: it starts `skip` time units after the minimum of ln E (where
+    the seeded perturbation has decayed into the growing mode) and ends at the
+    first sample where ln E has risen by `rise` above its value at the start,
+    or at the last sample.  gamma = half the least-squares slope of ln E over
+    those samples.  Returns (gamma, first, last) sample indices included."""
+    lnE = np.log(np.asarray(E, dtype=np.float64))
+    n = len(lnE)
+    t = np.arange(n) * dt_sample
+    first = min(n - 2, int(np.argmin(lnE)) + int(round(skip / dt_sample)))
+    last = first + 1
+    while last < n - 1 and lnE[last] < lnE[first] + rise:
+        last += 1
+    return 0.5 * ols_slope(t[first:last + 1], lnE[first:last + 1]), first, last

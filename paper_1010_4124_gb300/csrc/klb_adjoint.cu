@@ -30,8 +30,6 @@ struct klb_adj {
     std::vector<void*> ck;         // state at the start of each segment (full buffers)
     std::vector<void*> seg;        // states of one segment during the reverse sweep (ckpt - 1 extra)
     void* lam[2] = {nullptr, nullptr};
-    void* Dx = nullptr;
-    void* Dy = nullptr;
     void* Nb = nullptr;            // per-node f^(0) sensitivity and u_y (5 * nx * ny)
     double* fields = nullptr;      // the initial fields (4 * nx * ny)
     double* dense = nullptr;       // staging for host / dense arrays (19 * nx * ny)
@@ -78,27 +76,44 @@ static int raw_step(klb_adj_t* a) {
     return KLB_OK;
 }
 
+// tile rows of the fused reverse step: 8 (its shared memory in FP64 stays
+// within the static 48 KB)
+constexpr int kAdjRows = 8;
+
 template <typename T>
-static int vjp_step(klb_adj_t* a, const void* f, const void* lam_in, void* lam_out, double coef) {
+static int vjp_step(klb_adj_t* a, const void* f, void* lam_in, void* lam_out, double coef) {
     klb_t* h = a->h;
     const StepConst<T>& c = *reinterpret_cast<const StepConst<T>*>(sizeof(T) == 8 ? (const void*)&h->cd
                                                                                    : (const void*)&h->cf);
     const Geom& g = h->g;
-    // one thread per (face, velocity) and per (node, velocity)
     const long long n = (long long)g.nx * g.ny;
-    const long long nfmax = std::max((long long)(g.nx + 1) * g.ny, (long long)g.nx * (g.ny + 1));
-    // face gradients and node sensitivities (independent), then the gather
-    adj_faces_kernel<T><<<dim3(grid_of(std::max(nfmax, n)), (NQ - 1) + 12 + 1), 256, 0, h->stream>>>(
-        c, g, (const T*)f, (const T*)lam_in, (T*)a->Dx, (T*)a->Dy, (T*)a->Nb);
-    adj_gather_kernel<T><<<dim3(grid_of(n), NQ), 256, 0, h->stream>>>(
-        c, g, (const T*)lam_in, (const T*)a->Nb, (const T*)a->Dx, (const T*)a->Dy, T(coef), (T*)lam_out);
+    // fold lambda^{n+1}'s ghost sums into its nodes and form the per-node
+    // f^(0) sensitivities; then the fused faces-and-gather pass
+    adj_node_kernel<T, true><<<grid_of(n), 256, 0, h->stream>>>(c, g, (const T*)f, (T*)lam_in, (T*)a->Nb);
+    const long long tiles = (long long)AdjTile<kAdjRows>::tiles_x(g.nx) * AdjTile<kAdjRows>::tiles_y(g.ny);
+    adj_tile_kernel<T, kAdjRows><<<dim3((unsigned)tiles, NQ), 32 * kAdjRows, 0, h->stream>>>(
+        c, g, (const T*)f, (const T*)lam_in, (const T*)a->Nb, T(coef), (T*)lam_out);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return afail(a, KLB_E_CUDA, std::string("adjoint kernels: ") + cudaGetErrorString(e));
     h->launches += 2;
     return KLB_OK;
 }
 
-static int vjp(klb_adj_t* a, const void* f, const void* lam_in, void* lam_out, double coef) {
+// the ghost sums of the last lambda folded into its nodes
+template <typename T>
+static int fold(klb_adj_t* a, void* lam) {
+    klb_t* h = a->h;
+    const StepConst<T>& c = *reinterpret_cast<const StepConst<T>*>(sizeof(T) == 8 ? (const void*)&h->cd
+                                                                                   : (const void*)&h->cf);
+    adj_node_kernel<T, false><<<grid_of((long long)h->g.nx * h->g.ny), 256, 0, h->stream>>>(c, h->g, nullptr,
+                                                                                             (T*)lam, nullptr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return afail(a, KLB_E_CUDA, std::string("adjoint fold: ") + cudaGetErrorString(e));
+    h->launches += 1;
+    return KLB_OK;
+}
+
+static int vjp(klb_adj_t* a, const void* f, void* lam_in, void* lam_out, double coef) {
     return a->h->p.precision == KLB_FP64 ? vjp_step<double>(a, f, lam_in, lam_out, coef)
                                          : vjp_step<float>(a, f, lam_in, lam_out, coef);
 }
@@ -175,7 +190,7 @@ static int reverse(klb_adj_t* a, bool sources, double g_ke, double g_gamma, int*
         }
     }
     *lam_cur = lc;
-    return KLB_OK;
+    return a->h->p.precision == KLB_FP64 ? fold<double>(a, a->lam[lc]) : fold<float>(a, a->lam[lc]);
 }
 
 template <typename T>
@@ -226,8 +241,6 @@ int klb_adjoint_create(const klb_params* p, int64_t nsteps, int32_t checkpoint_e
     a->seg.assign(std::max(0, a->ckpt - 1), nullptr);
     for (size_t s = 0; s < a->seg.size() && ok; ++s) ok = cudaMalloc(&a->seg[s], sb) == cudaSuccess;
     for (int k = 0; k < 2 && ok; ++k) ok = cudaMalloc(&a->lam[k], sb) == cudaSuccess;
-    ok = ok && cudaMalloc(&a->Dx, h->esize * 5 * (size_t)18 * h->g.ny * (h->g.nx + 1)) == cudaSuccess;
-    ok = ok && cudaMalloc(&a->Dy, h->esize * 5 * (size_t)12 * (h->g.ny + 1) * h->g.nx) == cudaSuccess;
     ok = ok && cudaMalloc(&a->Nb, h->esize * 5 * nn) == cudaSuccess;
     ok = ok && cudaMalloc(&a->fields, sizeof(double) * 4 * nn) == cudaSuccess;
     ok = ok && cudaMalloc(&a->dense, sizeof(double) * NQ * nn) == cudaSuccess;
@@ -250,8 +263,6 @@ void klb_adjoint_destroy(klb_adj_t* a) {
         if (p) cudaFree(p);
     for (int k = 0; k < 2; ++k)
         if (a->lam[k]) cudaFree(a->lam[k]);
-    if (a->Dx) cudaFree(a->Dx);
-    if (a->Dy) cudaFree(a->Dy);
     if (a->Nb) cudaFree(a->Nb);
     if (a->fields) cudaFree(a->fields);
     if (a->dense) cudaFree(a->dense);

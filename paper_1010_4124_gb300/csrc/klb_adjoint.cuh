@@ -178,100 +178,6 @@ __device__ __forceinline__ int yslot_of(int q) {
     return 4 * (ring_of(q) - 1) + (d < 3 ? d - 1 : d - 2);
 }
 
-// Face-gradient buffers, structure of arrays: entry k of the face at
-// position t of velocity slot s lives at D[(5 s + k) nf + t].
-// x faces: thread t = (i, j), i in [0, nx] the face between nodes i-1 and i
-// of row j, for velocity q = blockIdx.y + 1 (every moving velocity has
-// v_x != 0): the five entries mu * v * dh/dF.
-template <typename T>
-__device__ __forceinline__ void adj_faces_x(const StepConst<T>& c, const Geom& g, const T* __restrict__ f,
-                                            const T* __restrict__ lam, T* __restrict__ D, int qx) {
-    const long long nf = (long long)(g.nx + 1) * g.ny;
-    const int q = qx + 1;
-    const T v = c.vx[q];
-    T* __restrict__ out = D + (long long)(5 * qx) * nf;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nf; t += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(t % (g.nx + 1)), j = (int)(t / (g.nx + 1));
-        const T* row = f + q * g.plane + (long long)(j + GY) * g.px + GX;
-        T a, b, cc, d, e;
-        if (v > 0) {
-            a = v * row[i - 3]; b = v * row[i - 2]; cc = v * row[i - 1]; d = v * row[i]; e = v * row[i + 1];
-        } else {
-            a = v * row[i + 2]; b = v * row[i + 1]; cc = v * row[i]; d = v * row[i - 1]; e = v * row[i - 2];
-        }
-        T gr[5];
-        weno5_grad(a, b, cc, d, e, c.eps, gr);
-        const T mu = c.dt / c.dx * (lam_at(lam, g, q, i, j) - lam_at(lam, g, q, i - 1, j)) * v;
-#pragma unroll
-        for (int k = 0; k < 5; ++k) out[k * nf + t] = mu * gr[k];
-    }
-}
-
-// y faces: thread t = (i, j), j in [0, ny] the face between rows j-1 and j of
-// column i, for the velocity of y slot blockIdx.y
-template <typename T>
-__device__ __forceinline__ void adj_faces_y(const StepConst<T>& c, const Geom& g, const T* __restrict__ f,
-                                            const T* __restrict__ lam, T* __restrict__ D, int qy) {
-    const long long nf = (long long)g.nx * (g.ny + 1);
-    const int q = yvel_of(qy);
-    const T v = c.vy[q];
-    T* __restrict__ out = D + (long long)(5 * qy) * nf;
-    const long long P = g.px;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nf; t += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(t % g.nx), j = (int)(t / g.nx);
-        const T* col = f + q * g.plane + (long long)GY * g.px + (i + GX);
-        T a, b, cc, d, e;
-        if (v > 0) {
-            a = v * col[(j - 3) * P]; b = v * col[(j - 2) * P]; cc = v * col[(j - 1) * P];
-            d = v * col[j * P]; e = v * col[(j + 1) * P];
-        } else {
-            a = v * col[(j + 2) * P]; b = v * col[(j + 1) * P]; cc = v * col[j * P];
-            d = v * col[(j - 1) * P]; e = v * col[(j - 2) * P];
-        }
-        T gr[5];
-        weno5_grad(a, b, cc, d, e, c.eps, gr);
-        const T mu = c.dt / c.dy * (lam_at(lam, g, q, i, j) - lam_at(lam, g, q, i, j - 1)) * v;
-#pragma unroll
-        for (int k = 0; k < 5; ++k) out[k * nf + t] = mu * gr[k];
-    }
-}
-
-// Per node: the sensitivity of f^(0) carried to the moments (four values,
-// feq_vjp_moments) and u_y (for the source term), into N[5][nx * ny].
-template <typename T>
-__device__ __forceinline__ void adj_node(const StepConst<T>& c, const Geom& g, const T* __restrict__ f,
-                                         const T* __restrict__ lam, T* __restrict__ N) {
-    const long long n = (long long)g.nx * g.ny;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(t % g.nx), j = (int)(t / g.nx);
-        const long long at = (long long)(j + GY) * g.px + (i + GX);
-        T fl[NQ], ll[NQ];
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            fl[q] = f[q * g.plane + at];
-            ll[q] = lam[q * g.plane + at];
-        }
-        const Mom<T> m = moments_of(c, fl);
-        T gm[4];
-        feq_vjp_moments(c, m, ll, gm);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) N[k * n + t] = gm[k];
-        N[4 * n + t] = m.uy;
-    }
-}
-
-// Everything of a reverse step that reads only f^n and lambda^{n+1}, in one
-// launch: blockIdx.y < 18 the x faces of velocity blockIdx.y + 1, 18 .. 29 the
-// y faces of y slot blockIdx.y - 18, 30 the per-node moment sensitivities.
-template <typename T>
-__global__ void adj_faces_kernel(const StepConst<T> c, const Geom g, const T* __restrict__ f,
-                                 const T* __restrict__ lam, T* __restrict__ Dx, T* __restrict__ Dy,
-                                 T* __restrict__ N) {
-    if (blockIdx.y < NQ - 1) adj_faces_x(c, g, f, lam, Dx, (int)blockIdx.y);
-    else if (blockIdx.y < NQ - 1 + 12) adj_faces_y(c, g, f, lam, Dy, (int)blockIdx.y - (NQ - 1));
-    else adj_node(c, g, f, lam, N);
-}
-
 // stencil positions that hold node i's value: the node itself and, next to a
 // periodic or outflow side, its ghost images (a fixed-equilibrium ghost is a
 // constant and carries no sensitivity)
@@ -298,56 +204,196 @@ __device__ __forceinline__ int images(int i, int n, int per, int lo_out, int hi_
     return m;
 }
 
-// lambda^n at interior node t = (i, j) for velocity q = blockIdx.y: the BGK
-// adjoint, the gathered face entries and, with coef != 0, the source
-// coef * dK/df of K = sum rho u_y^2 / 2.
-template <typename T>
-__global__ void adj_gather_kernel(const StepConst<T> c, const Geom g, const T* __restrict__ lam,
-                                  const T* __restrict__ N, const T* __restrict__ Dx, const T* __restrict__ Dy,
-                                  T coef, T* __restrict__ lam_out) {
+// ---------------------------------------------------------------------------
+// The reverse step in two launches.
+//
+// lambda^n_q(p) = (1 - dt/tau) lambda^{n+1}_q(p)
+//               + dt/tau sum_r lambda^{n+1}_r(p) d f^(0)_r(p) / d f_q(p)      (BGK, Eq. 28)
+//               + sum over the faces whose WENO5 stencil holds p of
+//                 mu(face) dh(face)/dF at p, mu = dt/dx v (lambda(right) - lambda(left))
+//               + the objective's source at sampled steps.
+// A face's stencil may hold a ghost position, which is an image of an
+// interior node (periodic wrap or outflow copy, Eqs. 57, 63-64): the tile
+// kernel leaves those sums in the ghost cells of lambda^n, and the node
+// kernel of the next reverse step (or the final fold) adds each ghost cell to
+// the interior node it images and clears it.  So lambda's ghost cells are
+// zero whenever a tile kernel reads them.
+// ---------------------------------------------------------------------------
+
+// Per interior node: fold the ghost-image sums of lambda into the node (and
+// clear them); with NODE, also the f^(0) sensitivity carried to the moments
+// (feq_vjp_moments, four values) and u_y into N[5][nx * ny].
+template <typename T, bool NODE>
+__global__ void adj_node_kernel(const StepConst<T> c, const Geom g, const T* __restrict__ f, T* __restrict__ lam,
+                                T* __restrict__ N) {
     const long long n = (long long)g.nx * g.ny;
-    const long long nfx = (long long)(g.nx + 1) * g.ny, nfy = (long long)g.nx * (g.ny + 1);
-    const int q = blockIdx.y;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(t % g.nx), j = (int)(t / g.nx);
-        const long long at = q * g.plane + (long long)(j + GY) * g.px + (i + GX);
+        const long long at = (long long)(j + GY) * g.px + (i + GX);
+        int px_[8], py_[8];
+        const int mx = images(i, g.nx, g.bcx_lo == 0, g.bcx_lo == 1, g.bcx_hi == 1, px_);
+        const int my = images(j, g.ny, g.bcy_lo == 0, g.bcy_lo == 1, g.bcy_hi == 1, py_);
+        T ll[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            T* L = lam + q * g.plane;
+            T v = L[at];
+            if (mx > 1 || my > 1) {
+                for (int a = 0; a < mx; ++a)
+                    if (px_[a] != i) {
+                        T* cell = L + (long long)(j + GY) * g.px + (px_[a] + GX);
+                        v += *cell;
+                        *cell = T(0);
+                    }
+                for (int a = 0; a < my; ++a)
+                    if (py_[a] != j) {
+                        T* cell = L + (long long)(py_[a] + GY) * g.px + (i + GX);
+                        v += *cell;
+                        *cell = T(0);
+                    }
+                L[at] = v;
+            }
+            ll[q] = v;
+        }
+        if (NODE) {
+            T fl[NQ];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) fl[q] = f[q * g.plane + at];
+            const Mom<T> m = moments_of(c, fl);
+            T gm[4];
+            feq_vjp_moments(c, m, ll, gm);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) N[k * n + t] = gm[k];
+            N[4 * n + t] = m.uy;
+        }
+    }
+}
+
+// Tiles of the reverse step: 32 x TY positions of the extended grid (columns
+// -4 .. nx + 2, rows -3 .. ny + 2: interior nodes and the ghost positions
+// whose sums the node kernel folds back).  One CTA per (tile, velocity q).
+template <int TY>
+struct AdjTile {
+    static constexpr int TX = 32;
+    static __host__ __device__ int tiles_x(int nx) { return (nx + GX + 3 + TX - 1) / TX; }
+    static __host__ __device__ int tiles_y(int ny) { return (ny + 2 * GY + TY - 1) / TY; }
+};
+
+// One CTA: velocity q = blockIdx.y on tile blockIdx.x.  f^n_q is staged with
+// a halo of 5 positions (the stencils of the faces within 3 of the tile), and
+// lambda^{n+1}_q with a halo of 3 (the faces' mu); every face whose stencil
+// reaches the tile is evaluated once into shared memory (the 5 entries
+// mu dh/dF), and each position gathers the entries that touch it.
+template <typename T, int TY>
+__global__ void __launch_bounds__(32 * TY) adj_tile_kernel(const StepConst<T> c, const Geom g, const T* __restrict__ f,
+                                                           const T* __restrict__ lam, const T* __restrict__ N, T coef,
+                                                           T* __restrict__ lam_out) {
+    constexpr int TX = AdjTile<TY>::TX;
+    __shared__ T fs[TY + 10][TX + 10];  // positions (y0 - 5 + r, x0 - 5 + s)
+    __shared__ T ls[TY + 6][TX + 6];    // positions (y0 - 3 + r, x0 - 3 + s)
+    __shared__ T gx[5][TY][TX + 5];     // x face i = x0 - 2 + s of row y0 + r
+    __shared__ T gy[5][TY + 5][TX];     // y face j = y0 - 2 + s of column x0 + l
+    const int q = blockIdx.y;
+    const int tiles_x = AdjTile<TY>::tiles_x(g.nx);
+    const int x0 = (int)(blockIdx.x % tiles_x) * TX - GX;
+    const int y0 = (int)(blockIdx.x / tiles_x) * TY - GY;
+    const int tid = threadIdx.x, l = tid & 31, w = tid >> 5;
+    const T* F = f + q * g.plane;
+    const T* L = lam + q * g.plane;
+    const T vx = c.vx[q], vy = c.vy[q];
+
+    for (int k = tid; k < (TY + 10) * (TX + 10); k += 32 * TY) {
+        const int r = k / (TX + 10), s = k - r * (TX + 10);
+        const int y = y0 - 5 + r, x = x0 - 5 + s;
+        const bool in = y >= -GY && y < g.ny + GY && x >= -GX && x < g.px - GX;
+        fs[r][s] = in ? F[(long long)(y + GY) * g.px + (x + GX)] : T(0);
+    }
+    for (int k = tid; k < (TY + 6) * (TX + 6); k += 32 * TY) {
+        const int r = k / (TX + 6), s = k - r * (TX + 6);
+        const int y = y0 - 3 + r, x = x0 - 3 + s;
+        const bool in = y >= 0 && y < g.ny && x >= 0 && x < g.nx;  // ghosts are not state variables
+        ls[r][s] = in ? L[(long long)(y + GY) * g.px + (x + GX)] : T(0);
+    }
+    __syncthreads();
+    if (q > 0) {
+        const T cx = c.dt / c.dx;
+        for (int k = tid; k < TY * (TX + 5); k += 32 * TY) {
+            const int r = k / (TX + 5), s = k - r * (TX + 5);
+            const int i = x0 - 2 + s, y = y0 + r;
+            T gr[5] = {T(0), T(0), T(0), T(0), T(0)};
+            T mu = T(0);
+            if (i >= 0 && i <= g.nx && y >= 0 && y < g.ny) {
+                const T* row = &fs[r + 5][0];
+                if (vx > T(0))
+                    weno5_grad(vx * row[s], vx * row[s + 1], vx * row[s + 2], vx * row[s + 3], vx * row[s + 4], c.eps,
+                               gr);
+                else
+                    weno5_grad(vx * row[s + 5], vx * row[s + 4], vx * row[s + 3], vx * row[s + 2], vx * row[s + 1],
+                               c.eps, gr);
+                mu = cx * (ls[r + 3][s + 1] - ls[r + 3][s]) * vx;
+            }
+#pragma unroll
+            for (int e = 0; e < 5; ++e) gx[e][r][s] = mu * gr[e];
+        }
+        if (vy != T(0)) {
+            const T cy = c.dt / c.dy;
+            for (int k = tid; k < (TY + 5) * TX; k += 32 * TY) {
+                const int s = k / TX, ll = k - s * TX;
+                const int j = y0 - 2 + s, x = x0 + ll;
+                T gr[5] = {T(0), T(0), T(0), T(0), T(0)};
+                T mu = T(0);
+                if (j >= 0 && j <= g.ny && x >= 0 && x < g.nx) {
+                    const int cl = ll + 5;
+                    if (vy > T(0))
+                        weno5_grad(vy * fs[s][cl], vy * fs[s + 1][cl], vy * fs[s + 2][cl], vy * fs[s + 3][cl],
+                                   vy * fs[s + 4][cl], c.eps, gr);
+                    else
+                        weno5_grad(vy * fs[s + 5][cl], vy * fs[s + 4][cl], vy * fs[s + 3][cl], vy * fs[s + 2][cl],
+                                   vy * fs[s + 1][cl], c.eps, gr);
+                    mu = cy * (ls[s + 1][ll + 3] - ls[s][ll + 3]) * vy;
+                }
+#pragma unroll
+                for (int e = 0; e < 5; ++e) gy[e][s][ll] = mu * gr[e];
+            }
+        }
+    }
+    __syncthreads();
+    const int x = x0 + l, y = y0 + w;
+    const bool xin = x >= 0 && x < g.nx, yin = y >= 0 && y < g.ny;
+    const bool xg = (x >= -GX + 1 && x < 0) || (x >= g.nx && x < g.nx + 3);
+    const bool yg = (y >= -GY && y < 0) || (y >= g.ny && y < g.ny + 3);
+    if (!((xin && yin) || (xg && yin) || (xin && yg))) return;
+    T acc = T(0);
+    if (q > 0 && yin) {  // x faces whose stencil holds position x (its slot e in that stencil)
+        if (vx > T(0)) {
+#pragma unroll
+            for (int e = 0; e < 5; ++e) acc += gx[e][w][l + 5 - e];
+        } else {
+#pragma unroll
+            for (int e = 0; e < 5; ++e) acc += gx[e][w][l + e];
+        }
+    }
+    if (q > 0 && vy != T(0) && xin) {
+        if (vy > T(0)) {
+#pragma unroll
+            for (int e = 0; e < 5; ++e) acc += gy[e][w + 5 - e][l];
+        } else {
+#pragma unroll
+            for (int e = 0; e < 5; ++e) acc += gy[e][w + e][l];
+        }
+    }
+    const long long at = q * g.plane + (long long)(y + GY) * g.px + (x + GX);
+    if (xin && yin) {
+        const long long n = (long long)g.nx * g.ny, t = (long long)y * g.nx + x;
         const T gm0 = N[t], gm1 = N[n + t], gm2 = N[2 * n + t], gm3 = N[3 * n + t];
-        T acc = (T(1) - c.relax) * lam[at] +
-                c.relax * (gm0 + gm1 * c.vx[q] + gm2 * c.vy[q] + gm3 * T(0.5) * c.v2[q]);
+        T v = (T(1) - c.relax) * ls[w + 3][l + 3] + c.relax * (gm0 + gm1 * vx + gm2 * vy + gm3 * T(0.5) * c.v2[q]);
         if (coef != T(0)) {
             const T uy = N[4 * n + t];
-            acc += coef * (uy * c.vy[q] - T(0.5) * uy * uy);
+            v += coef * (uy * vy - T(0.5) * uy * uy);
         }
-        if (q > 0) {
-            int pos_[8];
-            const int np = images(i, g.nx, g.bcx_lo == 0, g.bcx_lo == 1, g.bcx_hi == 1, pos_);
-            const T* Dq = Dx + (long long)(5 * (q - 1)) * nfx + (long long)j * (g.nx + 1);
-            const bool pos = c.vx[q] > 0;
-            for (int a = 0; a < np; ++a) {
-                const int p = pos_[a];
-                // faces i' whose stencil holds position p, and p's slot k in it
-                const int lo = pos ? p - 1 : p - 2, hi = pos ? p + 3 : p + 2;
-                for (int ip = (lo < 0 ? 0 : lo); ip <= (hi > g.nx ? g.nx : hi); ++ip) {
-                    const int k = pos ? p - ip + 3 : ip + 2 - p;
-                    acc += Dq[k * nfx + ip];
-                }
-            }
-        }
-        if (c.vy[q] != T(0)) {
-            int pos_[8];
-            const int np = images(j, g.ny, g.bcy_lo == 0, g.bcy_lo == 1, g.bcy_hi == 1, pos_);
-            const T* Dq = Dy + (long long)(5 * yslot_of(q)) * nfy + i;
-            const bool pos = c.vy[q] > 0;
-            for (int a = 0; a < np; ++a) {
-                const int p = pos_[a];
-                const int lo = pos ? p - 1 : p - 2, hi = pos ? p + 3 : p + 2;
-                for (int jp = (lo < 0 ? 0 : lo); jp <= (hi > g.ny ? g.ny : hi); ++jp) {
-                    const int k = pos ? p - jp + 3 : jp + 2 - p;
-                    acc += Dq[k * nfy + (long long)jp * g.nx];
-                }
-            }
-        }
-        lam_out[at] = acc;
+        lam_out[at] = v + acc;
+    } else {
+        lam_out[at] = acc;  // a ghost position: its sum waits for the fold
     }
 }
 

@@ -55,10 +55,16 @@ def problems(name: str, steps: int = 40000, sample_every: int = 50):
     return [inputs.paper_khi(Dv, Dr, state, steps=steps, sample_every=sample_every) for Dv, Dr in pairs]
 
 
-def run(name: str, steps: int = 40000, sample_every: int = 50, stream=None):
+def run(name: str, steps: int = 40000, sample_every: int = 50, stream=None, dv=None):
     """Run the sweep `name` as one batch (all instances advance together, one
-    persistent launch per step) and fit each instance's growth rate."""
+    persistent launch per step) and fit each instance's growth rate.  For the
+    density study, `dv` replaces the fixed D_v (cells) that the paper leaves
+    unstated; "equal" sets D_v = D_rho for every instance."""
     state, pairs = SWEEPS[name]
+    if dv is not None:
+        if name != "density":
+            raise ValueError("dv applies to the density study only")
+        pairs = [(Dr if dv == "equal" else float(dv), Dr) for _, Dr in pairs]
     return run_pairs(state, pairs, steps, sample_every, stream)
 
 
@@ -110,8 +116,10 @@ def main(argv=None):
     ap.add_argument("study", choices=sorted(SWEEPS))
     ap.add_argument("--steps", type=int, default=40000)
     ap.add_argument("--sample-every", type=int, default=50)
+    ap.add_argument("--dv", default=None,
+                    help="density study only: the fixed D_v in cells (default 4), or 'equal' for D_v = D_rho")
     args = ap.parse_args(argv)
-    res = run(args.study, steps=args.steps, sample_every=args.sample_every)
+    res = run(args.study, steps=args.steps, sample_every=args.sample_every, dv=args.dv)
     for r in res:
         print(f"D_v = {r['Dv']:6.2f}  D_rho = {r['Drho']:6.2f}  R = {r['R']:5.2f}  gamma = {r['gamma']:.4f}")
     if args.study == "velocity":

@@ -120,30 +120,63 @@ def test_fp32_adjoint_close_to_fp64():
         assert np.abs(a - b).max() <= 2e-3 * scale
 
 
+def _khi256():
+    return inputs.khi(256, 256, 2000, Dv=4.0, Drho=4.0, sample_every=10)
+
+
+def _width_gradients(pb, fields, d_rho, d_ux, d_T):
+    """d/dD_v and d/dD_rho of an objective from its gradients with respect to
+    the initial fields (the chain rule through the tanh profiles)."""
+    X, Y = inputs.coords(pb)
+    s = Y / (pb.Dv * pb.dy)
+    dux = 0.5 * pb.u0 / np.cosh(s) ** 2 * (-s / pb.Dv)
+    sr = Y / (pb.Drho * pb.dy)
+    drho = 0.5 * (pb.rho1 - pb.rho2) / np.cosh(sr) ** 2 * (-sr / pb.Drho)
+    rho = fields[0]
+    return float((d_ux * dux).sum()), float((d_rho * drho + d_T * (-pb.p0 / rho**2) * drho).sum())
+
+
 def test_config_size_gradient_vs_finite_differences():
     # 256 x 256 KHI as the single run, 2000 steps, checkpoints every 45:
-    # dKE/dD_v and dKE/dD_rho by the adjoint against central differences of
-    # the GPU forward in FP64 (h = 1e-4)
-    pb = inputs.khi(256, 256, 2000, Dv=4.0, Drho=4.0, sample_every=10)
+    # dKE/dD_v, dKE/dD_rho, dgamma/dD_v and dgamma/dD_rho by the adjoint
+    # against central differences of the GPU forward in FP64 (h = 1e-4)
+    pb = _khi256()
     with klb.KlbAdjoint.from_problem(pb, "fp64", checkpoint_every=45) as adj:
         fields = inputs.fields(pb)
         adj.forward(*fields)
-        d_rho, d_ux, d_uy, d_T = adj.backward(1.0, 0.0)
-        X, Y = inputs.coords(pb)
-        s = Y / (pb.Dv * pb.dy)
-        dux = 0.5 * pb.u0 / np.cosh(s) ** 2 * (-s / pb.Dv)
-        g_dv = float((d_ux * dux).sum())
-        sr = Y / (pb.Drho * pb.dy)
-        drho = 0.5 * (pb.rho1 - pb.rho2) / np.cosh(sr) ** 2 * (-sr / pb.Drho)
-        rho = fields[0]
-        g_dr = float((d_rho * drho + d_T * (-pb.p0 / rho**2) * drho).sum())
+        d_rho, d_ux, _, d_T = adj.backward(1.0, 0.0)
+        g_ke = _width_gradients(pb, fields, d_rho, d_ux, d_T)
+        d_rho, d_ux, _, d_T = adj.backward(0.0, 1.0)
+        g_gamma = _width_gradients(pb, fields, d_rho, d_ux, d_T)
         h = 1e-4
-        fd = []
+        fd_ke, fd_gamma = [], []
         for key in ("Dv", "Drho"):
-            vals = []
-            for sgn in (1, -1):
-                kw = {key: getattr(pb, key) + sgn * h}
-                vals.append(adj.forward(*inputs.fields(pb, **kw))[0])
-            fd.append((vals[0] - vals[1]) / (2 * h))
-    assert g_dv == pytest.approx(fd[0], rel=1e-5)
-    assert g_dr == pytest.approx(fd[1], rel=1e-5)
+            vals = [adj.forward(*inputs.fields(pb, **{key: getattr(pb, key) + sgn * h})) for sgn in (1, -1)]
+            fd_ke.append((vals[0][0] - vals[1][0]) / (2 * h))
+            fd_gamma.append((vals[0][1] - vals[1][1]) / (2 * h))
+    assert g_ke[0] == pytest.approx(fd_ke[0], rel=1e-5)
+    assert g_ke[1] == pytest.approx(fd_ke[1], rel=1e-5)
+    assert g_gamma[0] == pytest.approx(fd_gamma[0], rel=1e-5)
+    assert g_gamma[1] == pytest.approx(fd_gamma[1], rel=1e-5)
+
+
+def test_config_size_uy0_gradient_along_random_directions():
+    # the same run: the adjoint's gradient of KE with respect to the initial
+    # u_y field, projected on 16 seeded random directions (8 white-noise
+    # fields, 8 with the perturbation's Gaussian envelope), against central
+    # differences of the GPU forward along each direction (FP64, h = 1e-4)
+    pb = _khi256()
+    rng = np.random.default_rng(256)
+    env = np.exp(-(inputs.coords(pb)[1] / (0.05 * pb.ny * pb.dy)) ** 2)
+    dirs = [rng.standard_normal((pb.ny, pb.nx)) * (env if k >= 8 else 1.0) for k in range(16)]
+    fields = inputs.fields(pb)
+    uy0 = fields[2]
+    h = 1e-4
+    with klb.KlbAdjoint.from_problem(pb, "fp64", checkpoint_every=45) as adj:
+        adj.forward(*fields)
+        _, _, d_uy, _ = adj.backward(1.0, 0.0)
+        for k, dvec in enumerate(dirs):
+            got = float((d_uy * dvec).sum())
+            ke = [adj.forward(*inputs.fields(pb, uy=uy0 + sgn * h * dvec))[0] for sgn in (1, -1)]
+            fd = (ke[0] - ke[1]) / (2 * h)
+            assert got == pytest.approx(fd, rel=1e-5), (k, got, fd)

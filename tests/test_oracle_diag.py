@@ -47,3 +47,21 @@ def test_mean_density_profile_by_brute_force_and_mass():
     # a state uniform along x gives back its rows (to the rounding of nx equal terms over nx)
     g = np.repeat(f[:, :, :1], p.nx, axis=2)
     np.testing.assert_allclose(core.mean_density(p, g), g[:, :, 0].sum(axis=0), rtol=1e-15)
+
+
+@pytest.mark.parametrize("gamma", [3.0, 9.5])
+def test_linear_stage_rate_recovers_a_planted_exponent(gamma):
+    # a decay into exp(2 gamma t) that saturates later (the shape of E_max in
+    # Sec. IV.A): the fitted rate is the planted one, the window starts 0.05
+    # after the minimum and stops once ln E has risen by 4 (before saturation)
+    dt = 5e-4
+    t = np.arange(2000) * dt
+    lnE = np.where(t < 0.1, -6.0 - 30.0 * t, -9.0 + 2.0 * gamma * (t - 0.1))
+    lnE = np.minimum(lnE, -2.0)
+    g, first, last = fit.linear_stage_rate(np.exp(lnE), dt)
+    assert g == pytest.approx(gamma, rel=1e-10)
+    assert first == 200 + 100
+    assert lnE[last] >= lnE[first] + 4.0 and lnE[last - 1] < lnE[first] + 4.0 and lnE[last] < -2.0
+    # a run that ends inside the growth: the window reaches the last sample
+    g2, _, last2 = fit.linear_stage_rate(np.exp(lnE[:400]), dt)
+    assert g2 == pytest.approx(gamma, rel=1e-10) and last2 == 399
