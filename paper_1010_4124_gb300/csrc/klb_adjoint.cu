@@ -357,13 +357,19 @@ int klb_adjoint_vjp(klb_adj_t* a, const double* lam_N, double* lam_0, int on_dev
     if (!a->forward_done) return afail(a, KLB_E_STATE, "klb_adjoint_vjp before klb_adjoint_forward");
     klb_t* h = a->h;
     const size_t nn = (size_t)h->g.nx * h->g.ny;
-    // lambda^N into the padded layout, through the f import kernel (ghosts unused)
+    // lambda^N into the interior of the padded layout, ghost cells zero
     ACK(a, cudaMemcpyAsync(a->dense, lam_N, sizeof(double) * NQ * nn,
                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
     ACK(a, cudaMemsetAsync(a->lam[0], 0, state_bytes(h), h->stream));
-    cudaError_t e = h->p.precision == KLB_FP64 ? launch_set_f<double>(h->g, a->dense, (double*)a->lam[0], h->stream)
-                                                : launch_set_f<float>(h->g, a->dense, (float*)a->lam[0], h->stream);
+    if (h->p.precision == KLB_FP64)
+        adj_import_kernel<double><<<grid_of((long long)(NQ * nn)), 256, 0, h->stream>>>(h->g, a->dense,
+                                                                                         (double*)a->lam[0]);
+    else
+        adj_import_kernel<float><<<grid_of((long long)(NQ * nn)), 256, 0, h->stream>>>(h->g, a->dense,
+                                                                                       (float*)a->lam[0]);
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return afail(a, KLB_E_CUDA, cudaGetErrorString(e));
+    h->launches += 1;
     int lc = 0;
     int r = reverse(a, false, 0.0, 0.0, &lc);
     if (r != KLB_OK) return r;

@@ -397,6 +397,20 @@ __global__ void __launch_bounds__(32 * TY) adj_tile_kernel(const StepConst<T> c,
     }
 }
 
+// lam := src[19][ny][nx] on the interior; the ghost cells stay zero (the
+// fold of the reverse sweep reads them as pending image sums)
+template <typename T>
+__global__ void adj_import_kernel(const Geom g, const double* __restrict__ src, T* __restrict__ lam) {
+    const long long n = (long long)g.nx * g.ny;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < NQ * n;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int q = (int)(t / n);
+        const long long r = t - q * n;
+        const int i = (int)(r % g.nx), j = (int)(r / g.nx);
+        lam[q * g.plane + (long long)(j + GY) * g.px + (i + GX)] = T(src[t]);
+    }
+}
+
 // lam = coef * dK/df (the sensitivity of the final state)
 template <typename T>
 __global__ void adj_source_kernel(const StepConst<T> c, const Geom g, const T* __restrict__ f, T coef,
