@@ -166,8 +166,8 @@ def test_config_size_gradient_vs_finite_differences():
 def test_config_size_uy0_gradient_along_random_directions():
     # the same run: the adjoint's gradient of KE with respect to the initial
     # u_y field, projected on 16 seeded random directions, against central
-    # differences of the GPU forward along each direction (FP64, h = 1e-4).
-    # The directions are smooth random fields (a few low Fourier modes of
+    # differences of the GPU forward along each direction (FP64, h = 1e-4,
+    # Richardson-extrapolated with 2h).  The directions are smooth random fields (a few low Fourier modes of
     # random amplitude and phase, max |d| = 1; 8 of them under the
     # perturbation's Gaussian envelope): a white-noise direction would move
     # the WENO weights off their smooth regime within h and put O(1e-4) of
@@ -193,6 +193,13 @@ def test_config_size_uy0_gradient_along_random_directions():
         _, _, d_uy, _ = adj.backward(1.0, 0.0)
         for k, dvec in enumerate(dirs):
             got = float((d_uy * dvec).sum())
-            ke = [adj.forward(*inputs.fields(pb, uy=uy0 + sgn * h * dvec))[0] for sgn in (1, -1)]
-            fd = (ke[0] - ke[1]) / (2 * h)
-            assert got == pytest.approx(fd, rel=1e-5), (k, got, fd)
+            # central differences with h and 2h; their Richardson combination
+            # removes the h^2 term (a direction almost orthogonal to the
+            # gradient has a small derivative against which that term is not
+            # small: 6e-5 of it for one of these with h alone)
+            cd = []
+            for step in (h, 2 * h):
+                ke = [adj.forward(*inputs.fields(pb, uy=uy0 + sgn * step * dvec))[0] for sgn in (1, -1)]
+                cd.append((ke[0] - ke[1]) / (2 * step))
+            fd = (4.0 * cd[0] - cd[1]) / 3.0
+            assert got == pytest.approx(fd, rel=1e-5), (k, got, fd, cd)
