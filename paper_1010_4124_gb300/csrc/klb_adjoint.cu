@@ -76,6 +76,9 @@ static int raw_step(klb_adj_t* a) {
     return KLB_OK;
 }
 
+// the node kernel: one CTA row per grid row, columns strided over 256 threads
+static dim3 node_grid(const Geom& g) { return dim3((unsigned)((g.nx + 255) / 256), (unsigned)g.ny); }
+
 // tile rows of the fused reverse step: 8 (its shared memory in FP64 stays
 // within the static 48 KB)
 constexpr int kAdjRows = 8;
@@ -86,10 +89,9 @@ static int vjp_step(klb_adj_t* a, const void* f, void* lam_in, void* lam_out, do
     const StepConst<T>& c = *reinterpret_cast<const StepConst<T>*>(sizeof(T) == 8 ? (const void*)&h->cd
                                                                                    : (const void*)&h->cf);
     const Geom& g = h->g;
-    const long long n = (long long)g.nx * g.ny;
     // fold lambda^{n+1}'s ghost sums into its nodes and form the per-node
     // f^(0) sensitivities; then the fused faces-and-gather pass
-    adj_node_kernel<T, true><<<grid_of(n), 256, 0, h->stream>>>(c, g, (const T*)f, (T*)lam_in, (T*)a->Nb);
+    adj_node_kernel<T, true><<<node_grid(g), 256, 0, h->stream>>>(c, g, (const T*)f, (T*)lam_in, (T*)a->Nb);
     const long long tiles = (long long)AdjTile<kAdjRows>::tiles_x(g.nx) * AdjTile<kAdjRows>::tiles_y(g.ny);
     adj_tile_kernel<T, kAdjRows><<<dim3((unsigned)tiles, NQ), 32 * kAdjRows, 0, h->stream>>>(
         c, g, (const T*)f, (const T*)lam_in, (const T*)a->Nb, T(coef), (T*)lam_out);
@@ -105,8 +107,7 @@ static int fold(klb_adj_t* a, void* lam) {
     klb_t* h = a->h;
     const StepConst<T>& c = *reinterpret_cast<const StepConst<T>*>(sizeof(T) == 8 ? (const void*)&h->cd
                                                                                    : (const void*)&h->cf);
-    adj_node_kernel<T, false><<<grid_of((long long)h->g.nx * h->g.ny), 256, 0, h->stream>>>(c, h->g, nullptr,
-                                                                                             (T*)lam, nullptr);
+    adj_node_kernel<T, false><<<node_grid(h->g), 256, 0, h->stream>>>(c, h->g, nullptr, (T*)lam, nullptr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return afail(a, KLB_E_CUDA, std::string("adjoint fold: ") + cudaGetErrorString(e));
     h->launches += 1;

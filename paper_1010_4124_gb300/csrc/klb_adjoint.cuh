@@ -44,45 +44,39 @@ __device__ __forceinline__ void coeffs_and_slope(const StepConst<T>& c, T Tm, T 
 }
 
 // Gradient of the WENO5 flux h(a, b, c, d, e) (Eqs. 48-55) with respect to its
-// five inputs.  With alpha_q = delta_q / (eps + sigma_q)^2, S = sum alpha,
-// omega_q = alpha_q / S:
-//   dh/dx = sum_q omega_q dh_q/dx + sum_q beta_q dsigma_q/dx,
-//   beta_q = -2 alpha_q (h_q - h) / ((eps + sigma_q) S).
+// five inputs, in the difference form the FP32 step evaluates (its
+// derivation is in ArithF32::weno): with D1 = a - b, D2 = c - b, D3 = d - c,
+// E4 = d - e, the 3/4-scaled indicators s_q (eps34 = 3/4 eps), w_q = 1/s_q^2,
+// G1 = 5/6 D2 + 1/3 D1, G2 = D2 + 2 D3, G3 = 2 D3 + E4/2 and the weights
+// delta' = (1, 6, 3) (the optimal weights times 10),
+//   h = c + N / D,  N = sum G_q w_q,  D = sum delta'_q w_q,
+//   dh = dc + (1/D) [sum w_q dG_q + sum (G_q - delta'_q (h - c)) dw_q],
+//   dw_q = -2 w_q / s_q ds_q.
+// The partials with respect to (D1, D2, D3, E4) are mapped back to (a..e).
 template <typename T>
-__device__ __forceinline__ T weno5_grad(T a, T b, T c, T d, T e, T eps, T g[5]) {
-    const T r6 = T(1) / T(6);
-    const T h1 = (T(2) * a - T(7) * b + T(11) * c) * r6;
-    const T h2 = (-b + T(5) * c + T(2) * d) * r6;
-    const T h3 = (T(2) * c + T(5) * d - e) * r6;
-    const T t1 = a - T(2) * b + c, r1 = a - T(4) * b + T(3) * c;
-    const T t2 = b - T(2) * c + d, r2 = b - d;
-    const T t3 = c - T(2) * d + e, r3 = T(3) * c - T(4) * d + e;
-    const T k13 = T(13) / T(12);
-    const T s1 = eps + k13 * t1 * t1 + T(0.25) * r1 * r1;
-    const T s2 = eps + k13 * t2 * t2 + T(0.25) * r2 * r2;
-    const T s3 = eps + k13 * t3 * t3 + T(0.25) * r3 * r3;
-    // one reciprocal per indicator and one for the sum of the alphas
-    const T i1 = recip(s1), i2 = recip(s2), i3 = recip(s3);
-    const T al1 = T(0.1) * i1 * i1, al2 = T(0.6) * i2 * i2, al3 = T(0.3) * i3 * i3;
-    const T iS = recip(al1 + al2 + al3);
-    const T w1 = al1 * iS, w2 = al2 * iS, w3 = al3 * iS;
-    const T h = w1 * h1 + w2 * h2 + w3 * h3;
-    const T b1 = -T(2) * w1 * (h1 - h) * i1;
-    const T b2 = -T(2) * w2 * (h2 - h) * i2;
-    const T b3 = -T(2) * w3 * (h3 - h) * i3;
-    // dsigma_q/dx: d(13/12 t^2 + r^2/4) = 13/6 t dt + r/2 dr
-    const T k136 = T(13) / T(6);
-    const T u1 = k136 * t1, v1 = T(0.5) * r1;  // coefficients of dt1, dr1
-    const T u2 = k136 * t2, v2 = T(0.5) * r2;
-    const T u3 = k136 * t3, v3 = T(0.5) * r3;
-    // t1 = a - 2b + c, r1 = a - 4b + 3c ; t2 = b - 2c + d, r2 = b - d ; t3 = c - 2d + e, r3 = 3c - 4d + e
-    g[0] = w1 * (T(2) / T(6)) + b1 * (u1 + v1);
-    g[1] = w1 * (-T(7) / T(6)) + w2 * (-T(1) / T(6)) + b1 * (-T(2) * u1 - T(4) * v1) + b2 * (u2 + v2);
-    g[2] = w1 * (T(11) / T(6)) + w2 * (T(5) / T(6)) + w3 * (T(2) / T(6)) + b1 * (u1 + T(3) * v1) +
-           b2 * (-T(2) * u2) + b3 * (u3 + T(3) * v3);
-    g[3] = w2 * (T(2) / T(6)) + w3 * (T(5) / T(6)) + b2 * (u2 - v2) + b3 * (-T(2) * u3 - T(4) * v3);
-    g[4] = w3 * (-T(1) / T(6)) + b3 * (u3 + v3);
-    return h;
+__device__ __forceinline__ T weno5_grad(T a, T b, T c, T d, T e, T eps34, T g[5]) {
+    const T D1 = a - b, D2 = c - b, D3 = d - c, E4 = d - e;
+    const T s1 = D1 * (D1 + T(2.75) * D2) + T(2.5) * D2 * D2 + eps34;
+    const T s2 = D2 * (D2 - T(1.25) * D3) + D3 * D3 + eps34;
+    const T s3 = E4 * (E4 + T(2.75) * D3) + T(2.5) * D3 * D3 + eps34;
+    const T r1 = recip(s1), r2 = recip(s2), r3 = recip(s3);
+    const T w1 = r1 * r1, w2 = r2 * r2, w3 = r3 * r3;
+    const T G1 = T(5.0 / 6.0) * D2 + T(1.0 / 3.0) * D1, G2 = D2 + T(2) * D3, G3 = T(2) * D3 + T(0.5) * E4;
+    const T rD = recip(w1 + T(6) * w2 + T(3) * w3);
+    const T hh = (G1 * w1 + G2 * w2 + G3 * w3) * rD;  // h - c
+    const T o1 = w1 * rD, o2 = w2 * rD, o3 = w3 * rD;
+    const T m = T(-2) * rD;
+    const T b1 = m * (G1 - hh) * w1 * r1, b2 = m * (G2 - T(6) * hh) * w2 * r2, b3 = m * (G3 - T(3) * hh) * w3 * r3;
+    const T g1 = T(1.0 / 3.0) * o1 + b1 * (T(2) * D1 + T(2.75) * D2);
+    const T g2 = T(5.0 / 6.0) * o1 + o2 + b1 * (T(2.75) * D1 + T(5) * D2) + b2 * (T(2) * D2 - T(1.25) * D3);
+    const T g3 = T(2) * (o2 + o3) + b2 * (T(2) * D3 - T(1.25) * D2) + b3 * (T(2.75) * E4 + T(5) * D3);
+    const T g4 = T(0.5) * o3 + b3 * (T(2) * E4 + T(2.75) * D3);
+    g[0] = g1;
+    g[1] = -g1 - g2;
+    g[2] = T(1) + g2 - g3;
+    g[3] = g3 + g4;
+    g[4] = -g4;
+    return c + hh;
 }
 
 // Moments of one node (Eq. 10) in the form the derivatives use.
@@ -220,41 +214,83 @@ __device__ __forceinline__ int images(int i, int n, int per, int lo_out, int hi_
 // zero whenever a tile kernel reads them.
 // ---------------------------------------------------------------------------
 
-// Per interior node: fold the ghost-image sums of lambda into the node (and
-// clear them); with NODE, also the f^(0) sensitivity carried to the moments
-// (feq_vjp_moments, four values) and u_y into N[5][nx * ny].
+// The ghost-image sums of node (i, j) of one plane of lambda along x (ghost
+// cells of the same row) and along y (of the same column): added up and
+// cleared.  Periodic: ghost p images node p mod n; outflow: the three ghosts
+// beyond an edge node image it (fixed-equilibrium sides: the adjoint is not
+// offered for them).
+template <typename T>
+__device__ __forceinline__ T take_images(T* __restrict__ L, const Geom& g, int i, int j) {
+    T s = T(0);
+    const long long row = (long long)(j + GY) * g.px;
+    if (g.bcx_lo == 0) {
+#pragma unroll
+        for (int m = -3; m <= 3; ++m) {
+            const int p = i + m * g.nx;
+            if (m != 0 && ((p >= -3 && p < 0) || (p >= g.nx && p < g.nx + 3))) {
+                s += L[row + p + GX];
+                L[row + p + GX] = T(0);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int d = 1; d <= 3; ++d) {
+            if (i == 0 && g.bcx_lo == 1) {
+                s += L[row + GX - d];
+                L[row + GX - d] = T(0);
+            }
+            if (i == g.nx - 1 && g.bcx_hi == 1) {
+                s += L[row + g.nx + GX + d - 1];
+                L[row + g.nx + GX + d - 1] = T(0);
+            }
+        }
+    }
+    if (g.bcy_lo == 0) {
+#pragma unroll
+        for (int m = -3; m <= 3; ++m) {
+            const int p = j + m * g.ny;
+            if (m != 0 && ((p >= -3 && p < 0) || (p >= g.ny && p < g.ny + 3))) {
+                s += L[(long long)(p + GY) * g.px + i + GX];
+                L[(long long)(p + GY) * g.px + i + GX] = T(0);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int d = 1; d <= 3; ++d) {
+            if (j == 0 && g.bcy_lo == 1) {
+                s += L[(long long)(GY - d) * g.px + i + GX];
+                L[(long long)(GY - d) * g.px + i + GX] = T(0);
+            }
+            if (j == g.ny - 1 && g.bcy_hi == 1) {
+                s += L[(long long)(g.ny + GY + d - 1) * g.px + i + GX];
+                L[(long long)(g.ny + GY + d - 1) * g.px + i + GX] = T(0);
+            }
+        }
+    }
+    return s;
+}
+
+// Per interior node (row j = blockIdx.y, columns strided over the block):
+// fold the ghost-image sums of lambda into the node (and clear them); with
+// NODE, also the f^(0) sensitivity carried to the moments (feq_vjp_moments,
+// four values) and u_y into N[5][nx * ny].
 template <typename T, bool NODE>
-__global__ void adj_node_kernel(const StepConst<T> c, const Geom g, const T* __restrict__ f, T* __restrict__ lam,
-                                T* __restrict__ N) {
+__global__ void __launch_bounds__(256) adj_node_kernel(const StepConst<T> c, const Geom g, const T* __restrict__ f,
+                                                       T* __restrict__ lam, T* __restrict__ N) {
+    const int j = blockIdx.y;
     const long long n = (long long)g.nx * g.ny;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(t % g.nx), j = (int)(t / g.nx);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.nx; i += gridDim.x * blockDim.x) {
         const long long at = (long long)(j + GY) * g.px + (i + GX);
-        int px_[8], py_[8];
-        const int mx = images(i, g.nx, g.bcx_lo == 0, g.bcx_lo == 1, g.bcx_hi == 1, px_);
-        const int my = images(j, g.ny, g.bcy_lo == 0, g.bcy_lo == 1, g.bcy_hi == 1, py_);
+        if (has_images(g, i, j)) {  // a node next to a periodic or outflow side
+#pragma unroll 1
+            for (int q = 0; q < NQ; ++q) {
+                T* L = lam + q * g.plane;
+                L[at] += take_images(L, g, i, j);
+            }
+        }
         T ll[NQ];
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            T* L = lam + q * g.plane;
-            T v = L[at];
-            if (mx > 1 || my > 1) {
-                for (int a = 0; a < mx; ++a)
-                    if (px_[a] != i) {
-                        T* cell = L + (long long)(j + GY) * g.px + (px_[a] + GX);
-                        v += *cell;
-                        *cell = T(0);
-                    }
-                for (int a = 0; a < my; ++a)
-                    if (py_[a] != j) {
-                        T* cell = L + (long long)(py_[a] + GY) * g.px + (i + GX);
-                        v += *cell;
-                        *cell = T(0);
-                    }
-                L[at] = v;
-            }
-            ll[q] = v;
-        }
+        for (int q = 0; q < NQ; ++q) ll[q] = lam[q * g.plane + at];
         if (NODE) {
             T fl[NQ];
 #pragma unroll
@@ -262,6 +298,7 @@ __global__ void adj_node_kernel(const StepConst<T> c, const Geom g, const T* __r
             const Mom<T> m = moments_of(c, fl);
             T gm[4];
             feq_vjp_moments(c, m, ll, gm);
+            const long long t = (long long)j * g.nx + i;
 #pragma unroll
             for (int k = 0; k < 4; ++k) N[k * n + t] = gm[k];
             N[4 * n + t] = m.uy;
@@ -283,78 +320,87 @@ struct AdjTile {
 // a halo of 5 positions (the stencils of the faces within 3 of the tile), and
 // lambda^{n+1}_q with a halo of 3 (the faces' mu); every face whose stencil
 // reaches the tile is evaluated once into shared memory (the 5 entries
-// mu dh/dF), and each position gathers the entries that touch it.
+// mu dh/dF), and each position gathers the entries that touch it.  A face
+// outside the grid (i < 0 or i > nx, or a row outside it) has mu = 0, since
+// lambda is zero off the interior, so no face needs a validity test.
+// Threads map to faces in three fixed passes: x faces 0..31 of each row, y
+// faces 0..TY-1 of each column, then the remaining 5 y-face rows (warps
+// 0..4) and 5 x-face columns (warps 5.., 4 rows of 5 per warp).
 template <typename T, int TY>
 __global__ void __launch_bounds__(32 * TY) adj_tile_kernel(const StepConst<T> c, const Geom g, const T* __restrict__ f,
                                                            const T* __restrict__ lam, const T* __restrict__ N, T coef,
                                                            T* __restrict__ lam_out) {
     constexpr int TX = AdjTile<TY>::TX;
+    static_assert(TY >= 7, "the remainder pass needs warps 0..4 and two more");
     __shared__ T fs[TY + 10][TX + 10];  // positions (y0 - 5 + r, x0 - 5 + s)
     __shared__ T ls[TY + 6][TX + 6];    // positions (y0 - 3 + r, x0 - 3 + s)
     __shared__ T gx[5][TY][TX + 5];     // x face i = x0 - 2 + s of row y0 + r
     __shared__ T gy[5][TY + 5][TX];     // y face j = y0 - 2 + s of column x0 + l
     const int q = blockIdx.y;
     const int tiles_x = AdjTile<TY>::tiles_x(g.nx);
-    const int x0 = (int)(blockIdx.x % tiles_x) * TX - GX;
-    const int y0 = (int)(blockIdx.x / tiles_x) * TY - GY;
-    const int tid = threadIdx.x, l = tid & 31, w = tid >> 5;
+    const int by = (int)blockIdx.x / tiles_x;
+    const int x0 = ((int)blockIdx.x - by * tiles_x) * TX - GX;
+    const int y0 = by * TY - GY;
+    const int l = threadIdx.x & 31, w = threadIdx.x >> 5;
     const T* F = f + q * g.plane;
     const T* L = lam + q * g.plane;
     const T vx = c.vx[q], vy = c.vy[q];
 
-    for (int k = tid; k < (TY + 10) * (TX + 10); k += 32 * TY) {
-        const int r = k / (TX + 10), s = k - r * (TX + 10);
-        const int y = y0 - 5 + r, x = x0 - 5 + s;
-        const bool in = y >= -GY && y < g.ny + GY && x >= -GX && x < g.px - GX;
-        fs[r][s] = in ? F[(long long)(y + GY) * g.px + (x + GX)] : T(0);
+    for (int r = w; r < TY + 10; r += TY) {
+        const int y = y0 - 5 + r;
+        const bool yin = y >= -GY && y < g.ny + GY;
+        const T* row = F + (long long)(y + GY) * g.px + GX;
+        for (int s = l; s < TX + 10; s += 32) {
+            const int x = x0 - 5 + s;
+            fs[r][s] = (yin && x >= -GX && x < g.px - GX) ? row[x] : T(0);
+        }
     }
-    for (int k = tid; k < (TY + 6) * (TX + 6); k += 32 * TY) {
-        const int r = k / (TX + 6), s = k - r * (TX + 6);
-        const int y = y0 - 3 + r, x = x0 - 3 + s;
-        const bool in = y >= 0 && y < g.ny && x >= 0 && x < g.nx;  // ghosts are not state variables
-        ls[r][s] = in ? L[(long long)(y + GY) * g.px + (x + GX)] : T(0);
+    for (int r = w; r < TY + 6; r += TY) {
+        const int y = y0 - 3 + r;
+        const bool yin = y >= 0 && y < g.ny;  // ghosts are not state variables
+        const T* row = L + (long long)(y + GY) * g.px + GX;
+        for (int s = l; s < TX + 6; s += 32) {
+            const int x = x0 - 3 + s;
+            ls[r][s] = (yin && x >= 0 && x < g.nx) ? row[x] : T(0);
+        }
     }
     __syncthreads();
+    const T e34 = T(0.75) * c.eps;
+    // x face s of row r: stencil fs[r + 5][s .. s + 5] (upwind order by the
+    // sign of v_x), mu from lambda at columns s + 1 (right) and s (left)
+    auto face_x = [&](int r, int s) {
+        const T* row = &fs[r + 5][0];
+        T gr[5];
+        if (vx > T(0))
+            weno5_grad(vx * row[s], vx * row[s + 1], vx * row[s + 2], vx * row[s + 3], vx * row[s + 4], e34, gr);
+        else
+            weno5_grad(vx * row[s + 5], vx * row[s + 4], vx * row[s + 3], vx * row[s + 2], vx * row[s + 1], e34, gr);
+        const T mu = c.cx[q] * (ls[r + 3][s + 1] - ls[r + 3][s]);  // dt v_x / dx times the jump of lambda
+#pragma unroll
+        for (int e = 0; e < 5; ++e) gx[e][r][s] = mu * gr[e];
+    };
+    // y face s of column cl: stencil fs[s .. s + 5][cl + 5]
+    auto face_y = [&](int s, int cl) {
+        T gr[5];
+        const int x = cl + 5;
+        if (vy > T(0))
+            weno5_grad(vy * fs[s][x], vy * fs[s + 1][x], vy * fs[s + 2][x], vy * fs[s + 3][x], vy * fs[s + 4][x], e34,
+                       gr);
+        else
+            weno5_grad(vy * fs[s + 5][x], vy * fs[s + 4][x], vy * fs[s + 3][x], vy * fs[s + 2][x], vy * fs[s + 1][x],
+                       e34, gr);
+        const T mu = c.cy[q] * (ls[s + 1][cl + 3] - ls[s][cl + 3]);
+#pragma unroll
+        for (int e = 0; e < 5; ++e) gy[e][s][cl] = mu * gr[e];
+    };
     if (q > 0) {
-        const T cx = c.dt / c.dx;
-        for (int k = tid; k < TY * (TX + 5); k += 32 * TY) {
-            const int r = k / (TX + 5), s = k - r * (TX + 5);
-            const int i = x0 - 2 + s, y = y0 + r;
-            T gr[5] = {T(0), T(0), T(0), T(0), T(0)};
-            T mu = T(0);
-            if (i >= 0 && i <= g.nx && y >= 0 && y < g.ny) {
-                const T* row = &fs[r + 5][0];
-                if (vx > T(0))
-                    weno5_grad(vx * row[s], vx * row[s + 1], vx * row[s + 2], vx * row[s + 3], vx * row[s + 4], c.eps,
-                               gr);
-                else
-                    weno5_grad(vx * row[s + 5], vx * row[s + 4], vx * row[s + 3], vx * row[s + 2], vx * row[s + 1],
-                               c.eps, gr);
-                mu = cx * (ls[r + 3][s + 1] - ls[r + 3][s]) * vx;
-            }
-#pragma unroll
-            for (int e = 0; e < 5; ++e) gx[e][r][s] = mu * gr[e];
-        }
-        if (vy != T(0)) {
-            const T cy = c.dt / c.dy;
-            for (int k = tid; k < (TY + 5) * TX; k += 32 * TY) {
-                const int s = k / TX, ll = k - s * TX;
-                const int j = y0 - 2 + s, x = x0 + ll;
-                T gr[5] = {T(0), T(0), T(0), T(0), T(0)};
-                T mu = T(0);
-                if (j >= 0 && j <= g.ny && x >= 0 && x < g.nx) {
-                    const int cl = ll + 5;
-                    if (vy > T(0))
-                        weno5_grad(vy * fs[s][cl], vy * fs[s + 1][cl], vy * fs[s + 2][cl], vy * fs[s + 3][cl],
-                                   vy * fs[s + 4][cl], c.eps, gr);
-                    else
-                        weno5_grad(vy * fs[s + 5][cl], vy * fs[s + 4][cl], vy * fs[s + 3][cl], vy * fs[s + 2][cl],
-                                   vy * fs[s + 1][cl], c.eps, gr);
-                    mu = cy * (ls[s + 1][ll + 3] - ls[s][ll + 3]) * vy;
-                }
-#pragma unroll
-                for (int e = 0; e < 5; ++e) gy[e][s][ll] = mu * gr[e];
-            }
+        face_x(w, l);
+        if (vy != T(0)) face_y(w, l);
+        if (w < 5) {
+            if (vy != T(0)) face_y(TY + w, l);
+        } else if (l < 20) {
+            const int rr = 4 * (w - 5) + l / 5;
+            if (rr < TY) face_x(rr, TX + l % 5);
         }
     }
     __syncthreads();

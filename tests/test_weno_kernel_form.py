@@ -208,3 +208,42 @@ def test_product_form_fails_over_the_range():
     kinds = {(k, e) for k, e, _ in bad}
     assert ("uniform", 1e-10) in kinds  # (eps')^4 underflows: 0 * inf
     assert ("jump", 1e-6) in kinds      # sigma^4 of a jump of 1e5 overflows
+
+
+def grad_form(a, b, c, d, e, eps):
+    """The adjoint kernels' gradient of the flux with respect to (a, b, c, d, e)
+    (weno5_grad in klb_adjoint.cuh), in float64: partials with respect to the
+    differences D1 = a - b, D2 = c - b, D3 = d - c, E4 = d - e of
+    h = c + N / D (N = sum G_q w_q, D = w_1 + 6 w_2 + 3 w_3, w_q = 1 / s_q^2),
+    mapped back to the five values."""
+    e34 = 0.75 * eps
+    D1, D2, D3, E4 = a - b, c - b, d - c, d - e
+    s1 = D1 * (D1 + 2.75 * D2) + 2.5 * D2 * D2 + e34
+    s2 = D2 * (D2 - 1.25 * D3) + D3 * D3 + e34
+    s3 = E4 * (E4 + 2.75 * D3) + 2.5 * D3 * D3 + e34
+    r1, r2, r3 = 1 / s1, 1 / s2, 1 / s3
+    w1, w2, w3 = r1 * r1, r2 * r2, r3 * r3
+    G1, G2, G3 = 5 / 6 * D2 + 1 / 3 * D1, D2 + 2 * D3, 2 * D3 + 0.5 * E4
+    rD = 1 / (w1 + 6 * w2 + 3 * w3)
+    hh = (G1 * w1 + G2 * w2 + G3 * w3) * rD
+    o1, o2, o3 = w1 * rD, w2 * rD, w3 * rD
+    m = -2 * rD
+    b1, b2, b3 = m * (G1 - hh) * w1 * r1, m * (G2 - 6 * hh) * w2 * r2, m * (G3 - 3 * hh) * w3 * r3
+    g1 = o1 / 3 + b1 * (2 * D1 + 2.75 * D2)
+    g2 = 5 / 6 * o1 + o2 + b1 * (2.75 * D1 + 5 * D2) + b2 * (2 * D2 - 1.25 * D3)
+    g3 = 2 * (o2 + o3) + b2 * (2 * D3 - 1.25 * D2) + b3 * (2.75 * E4 + 5 * D3)
+    g4 = 0.5 * o3 + b3 * (2 * E4 + 2.75 * D3)
+    return c + hh, np.array([g1, -g1 - g2, 1 + g2 - g3, g3 + g4, -g4])
+
+
+@pytest.mark.parametrize("eps", [1e-6, 1e-3])
+def test_adjoint_gradient_form_equals_the_oracle_derivative(eps):
+    # the oracle's complex-step derivative of its own flux (Eqs. 48-55) is
+    # exact to rounding; the adjoint's difference-form gradient must match it
+    rng = np.random.default_rng(48)
+    hs = 1e-20
+    for F5 in _stencils(rng, 200):
+        h, g = grad_form(*F5, eps)
+        assert h == pytest.approx(core.weno5_face(F5, eps), rel=1e-11, abs=1e-13 * np.abs(F5).max())
+        ref = np.array([np.imag(core.weno5_face(F5 + 1j * hs * np.eye(5)[k], eps, cs=True)) / hs for k in range(5)])
+        assert np.abs(g - ref).max() <= 1e-11 * max(1.0, np.abs(ref).max()), (F5, g, ref)
