@@ -83,21 +83,30 @@ static dim3 node_grid(const Geom& g) { return dim3((unsigned)((g.nx + 255) / 256
 // within the static 48 KB)
 constexpr int kAdjRows = 8;
 
+// the ghost sums of lambda folded into the nodes they image
+template <typename T>
+static void launch_fold(const Geom& g, T* lam, cudaStream_t s) {
+    const int nbx = band_count(g.nx, g.bcx_lo, g.bcx_hi), nby = band_count(g.ny, g.bcy_lo, g.bcy_hi);
+    const long long work = (long long)NQ * ((long long)nbx * g.ny + (long long)nby * g.nx);
+    if (work > 0) adj_fold_kernel<T><<<grid_of(work), 256, 0, s>>>(g, lam, nbx, nby);
+}
+
 template <typename T>
 static int vjp_step(klb_adj_t* a, const void* f, void* lam_in, void* lam_out, double coef) {
     klb_t* h = a->h;
     const StepConst<T>& c = *reinterpret_cast<const StepConst<T>*>(sizeof(T) == 8 ? (const void*)&h->cd
                                                                                    : (const void*)&h->cf);
     const Geom& g = h->g;
-    // fold lambda^{n+1}'s ghost sums into its nodes and form the per-node
-    // f^(0) sensitivities; then the fused faces-and-gather pass
-    adj_node_kernel<T, true><<<node_grid(g), 256, 0, h->stream>>>(c, g, (const T*)f, (T*)lam_in, (T*)a->Nb);
+    // fold lambda^{n+1}'s ghost sums into its nodes, form the per-node f^(0)
+    // sensitivities, then the fused faces-and-gather pass
+    launch_fold<T>(g, (T*)lam_in, h->stream);
+    adj_node_kernel<T><<<node_grid(g), 256, 0, h->stream>>>(c, g, (const T*)f, (const T*)lam_in, (T*)a->Nb);
     const long long tiles = (long long)AdjTile<kAdjRows>::tiles_x(g.nx) * AdjTile<kAdjRows>::tiles_y(g.ny);
     adj_tile_kernel<T, kAdjRows><<<dim3((unsigned)tiles, NQ), 32 * kAdjRows, 0, h->stream>>>(
         c, g, (const T*)f, (const T*)lam_in, (const T*)a->Nb, T(coef), (T*)lam_out);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return afail(a, KLB_E_CUDA, std::string("adjoint kernels: ") + cudaGetErrorString(e));
-    h->launches += 2;
+    h->launches += 3;
     return KLB_OK;
 }
 
@@ -105,9 +114,7 @@ static int vjp_step(klb_adj_t* a, const void* f, void* lam_in, void* lam_out, do
 template <typename T>
 static int fold(klb_adj_t* a, void* lam) {
     klb_t* h = a->h;
-    const StepConst<T>& c = *reinterpret_cast<const StepConst<T>*>(sizeof(T) == 8 ? (const void*)&h->cd
-                                                                                   : (const void*)&h->cf);
-    adj_node_kernel<T, false><<<node_grid(h->g), 256, 0, h->stream>>>(c, h->g, nullptr, (T*)lam, nullptr);
+    launch_fold<T>(h->g, (T*)lam, h->stream);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return afail(a, KLB_E_CUDA, std::string("adjoint fold: ") + cudaGetErrorString(e));
     h->launches += 1;

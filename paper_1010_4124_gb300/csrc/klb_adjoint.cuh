@@ -208,101 +208,114 @@ __device__ __forceinline__ int images(int i, int n, int per, int lo_out, int hi_
 //               + the objective's source at sampled steps.
 // A face's stencil may hold a ghost position, which is an image of an
 // interior node (periodic wrap or outflow copy, Eqs. 57, 63-64): the tile
-// kernel leaves those sums in the ghost cells of lambda^n, and the node
-// kernel of the next reverse step (or the final fold) adds each ghost cell to
-// the interior node it images and clears it.  So lambda's ghost cells are
-// zero whenever a tile kernel reads them.
+// kernel leaves those sums in the ghost cells of lambda^n, and the fold
+// kernel of the next reverse step (or after the last one) adds each ghost
+// cell to the interior node it images and clears it.  So lambda's ghost
+// cells are zero whenever a tile kernel reads them.
 // ---------------------------------------------------------------------------
 
-// The ghost-image sums of node (i, j) of one plane of lambda along x (ghost
-// cells of the same row) and along y (of the same column): added up and
-// cleared.  Periodic: ghost p images node p mod n; outflow: the three ghosts
-// beyond an edge node image it (fixed-equilibrium sides: the adjoint is not
-// offered for them).
-template <typename T>
-__device__ __forceinline__ T take_images(T* __restrict__ L, const Geom& g, int i, int j) {
-    T s = T(0);
+// Ghost cells that image interior node (i, j): along x (cells of the same
+// row) and along y (of the same column).  Periodic: ghost p images node p mod
+// n; outflow: the three ghosts beyond an edge node image it (the adjoint is
+// not offered for fixed-equilibrium sides).  Up to 6 + 6 cells (grids
+// narrower than 3 nodes wrap several times); offsets into one plane.
+__device__ __forceinline__ int image_cells(const Geom& g, int i, int j, long long cell[12]) {
+    int m = 0;
     const long long row = (long long)(j + GY) * g.px;
     if (g.bcx_lo == 0) {
-#pragma unroll
-        for (int m = -3; m <= 3; ++m) {
-            const int p = i + m * g.nx;
-            if (m != 0 && ((p >= -3 && p < 0) || (p >= g.nx && p < g.nx + 3))) {
-                s += L[row + p + GX];
-                L[row + p + GX] = T(0);
-            }
+        for (int k = -3; k <= 3; ++k) {
+            const int p = i + k * g.nx;
+            if (k != 0 && ((p >= -3 && p < 0) || (p >= g.nx && p < g.nx + 3))) cell[m++] = row + p + GX;
         }
     } else {
-#pragma unroll
-        for (int d = 1; d <= 3; ++d) {
-            if (i == 0 && g.bcx_lo == 1) {
-                s += L[row + GX - d];
-                L[row + GX - d] = T(0);
-            }
-            if (i == g.nx - 1 && g.bcx_hi == 1) {
-                s += L[row + g.nx + GX + d - 1];
-                L[row + g.nx + GX + d - 1] = T(0);
-            }
-        }
+        if (i == 0 && g.bcx_lo == 1)
+            for (int d = 1; d <= 3; ++d) cell[m++] = row + GX - d;
+        if (i == g.nx - 1 && g.bcx_hi == 1)
+            for (int d = 0; d < 3; ++d) cell[m++] = row + g.nx + GX + d;
     }
     if (g.bcy_lo == 0) {
-#pragma unroll
-        for (int m = -3; m <= 3; ++m) {
-            const int p = j + m * g.ny;
-            if (m != 0 && ((p >= -3 && p < 0) || (p >= g.ny && p < g.ny + 3))) {
-                s += L[(long long)(p + GY) * g.px + i + GX];
-                L[(long long)(p + GY) * g.px + i + GX] = T(0);
-            }
+        for (int k = -3; k <= 3; ++k) {
+            const int p = j + k * g.ny;
+            if (k != 0 && ((p >= -3 && p < 0) || (p >= g.ny && p < g.ny + 3)))
+                cell[m++] = (long long)(p + GY) * g.px + i + GX;
         }
     } else {
-#pragma unroll
-        for (int d = 1; d <= 3; ++d) {
-            if (j == 0 && g.bcy_lo == 1) {
-                s += L[(long long)(GY - d) * g.px + i + GX];
-                L[(long long)(GY - d) * g.px + i + GX] = T(0);
-            }
-            if (j == g.ny - 1 && g.bcy_hi == 1) {
-                s += L[(long long)(g.ny + GY + d - 1) * g.px + i + GX];
-                L[(long long)(g.ny + GY + d - 1) * g.px + i + GX] = T(0);
-            }
-        }
+        if (j == 0 && g.bcy_lo == 1)
+            for (int d = 1; d <= 3; ++d) cell[m++] = (long long)(GY - d) * g.px + i + GX;
+        if (j == g.ny - 1 && g.bcy_hi == 1)
+            for (int d = 0; d < 3; ++d) cell[m++] = (long long)(g.ny + GY + d) * g.px + i + GX;
     }
-    return s;
+    return m;
 }
 
-// Per interior node (row j = blockIdx.y, columns strided over the block):
-// fold the ghost-image sums of lambda into the node (and clear them); with
-// NODE, also the f^(0) sensitivity carried to the moments (feq_vjp_moments,
-// four values) and u_y into N[5][nx * ny].
-template <typename T, bool NODE>
+// The columns (rows) whose nodes have x (y) images: the band next to a
+// periodic pair of sides (all of them on grids of at most 6), or the edge
+// nodes of outflow sides.  band_count gives their number, band_at the k-th.
+__host__ __device__ __forceinline__ int band_count(int n, int lo, int hi) {
+    if (lo == 0) return n < 6 ? n : 6;
+    return n == 1 ? ((lo == 1 || hi == 1) ? 1 : 0) : (lo == 1) + (hi == 1);
+}
+__host__ __device__ __forceinline__ int band_at(int n, int lo, int hi, int k) {
+    if (lo == 0) return n <= 6 ? k : (k < 3 ? k : n - 6 + k);
+    return (k == 0 && lo == 1) ? 0 : n - 1;
+}
+
+// Fold the ghost-image sums of lambda into the nodes they image (and clear
+// the ghost cells).  One thread per (node with images, velocity): first the
+// nodes of the x band (their y images too), then those of the y band that
+// have no x images.  All loads of a thread precede its stores.
+template <typename T>
+__global__ void adj_fold_kernel(const Geom g, T* __restrict__ lam, int nbx, int nby) {
+    const int nxb = nbx * g.ny, nyb = nby * g.nx, per_q = nxb + nyb;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < NQ * per_q; t += gridDim.x * blockDim.x) {
+        const int q = t / per_q, r = t - q * per_q;
+        int i, j;
+        if (r < nxb) {
+            j = r / nbx;
+            i = band_at(g.nx, g.bcx_lo, g.bcx_hi, r - j * nbx);
+        } else {
+            const int r2 = r - nxb;
+            const int k = r2 / g.nx;
+            i = r2 - k * g.nx;
+            j = band_at(g.ny, g.bcy_lo, g.bcy_hi, k);
+            const bool xe = g.bcx_lo == 0 ? (i < 3 || i >= g.nx - 3)
+                                          : ((i == 0 && g.bcx_lo == 1) || (i == g.nx - 1 && g.bcx_hi == 1));
+            if (xe) continue;  // folded with the x band
+        }
+        T* L = lam + q * g.plane;
+        long long cell[12];
+        const int m = image_cells(g, i, j, cell);
+        const long long at = (long long)(j + GY) * g.px + (i + GX);
+        T v = L[at];
+        for (int k = 0; k < m; ++k) v += L[cell[k]];
+        for (int k = 0; k < m; ++k) L[cell[k]] = T(0);
+        L[at] = v;
+    }
+}
+
+// Per interior node (row j = blockIdx.y, columns strided over the block), on
+// a folded lambda: the f^(0) sensitivity carried to the moments
+// (feq_vjp_moments, four values) and u_y into N[5][nx * ny].
+template <typename T>
 __global__ void __launch_bounds__(256) adj_node_kernel(const StepConst<T> c, const Geom g, const T* __restrict__ f,
-                                                       T* __restrict__ lam, T* __restrict__ N) {
+                                                       const T* __restrict__ lam, T* __restrict__ N) {
     const int j = blockIdx.y;
     const long long n = (long long)g.nx * g.ny;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.nx; i += gridDim.x * blockDim.x) {
         const long long at = (long long)(j + GY) * g.px + (i + GX);
-        if (has_images(g, i, j)) {  // a node next to a periodic or outflow side
-#pragma unroll 1
-            for (int q = 0; q < NQ; ++q) {
-                T* L = lam + q * g.plane;
-                L[at] += take_images(L, g, i, j);
-            }
+        T ll[NQ], fl[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            ll[q] = lam[q * g.plane + at];
+            fl[q] = f[q * g.plane + at];
         }
-        T ll[NQ];
+        const Mom<T> m = moments_of(c, fl);
+        T gm[4];
+        feq_vjp_moments(c, m, ll, gm);
+        const long long t = (long long)j * g.nx + i;
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) ll[q] = lam[q * g.plane + at];
-        if (NODE) {
-            T fl[NQ];
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) fl[q] = f[q * g.plane + at];
-            const Mom<T> m = moments_of(c, fl);
-            T gm[4];
-            feq_vjp_moments(c, m, ll, gm);
-            const long long t = (long long)j * g.nx + i;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) N[k * n + t] = gm[k];
-            N[4 * n + t] = m.uy;
-        }
+        for (int k = 0; k < 4; ++k) N[k * n + t] = gm[k];
+        N[4 * n + t] = m.uy;
     }
 }
 
