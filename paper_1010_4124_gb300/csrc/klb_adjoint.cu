@@ -15,12 +15,19 @@
 #include <algorithm>
 #include <cmath>
 #include <string>
+#include <deque>
 #include <vector>
 
 #include "klb_adjoint.cuh"
 #include "klb_handle.h"
 
 using namespace fdlb;
+
+struct AdjMap {  // a TMA map of one buffer for the tile kernel
+    const void* buf = nullptr;
+    int rows = 0;
+    CUtensorMap map;
+};
 
 struct klb_adj {
     klb_t* h = nullptr;            // forward grid (owns the step buffers)
@@ -33,6 +40,7 @@ struct klb_adj {
     void* Nb = nullptr;            // per-node f^(0) sensitivity and u_y (5 * nx * ny)
     double* fields = nullptr;      // the initial fields (4 * nx * ny)
     double* dense = nullptr;       // staging for host / dense arrays (19 * nx * ny)
+    std::deque<AdjMap> maps;       // the tile kernel's maps of the buffers above (stable addresses)
     std::vector<double> K;         // K_s of the forward run
     double ke = 0, gamma = 0;
     bool forward_done = false;
@@ -76,6 +84,19 @@ static int raw_step(klb_adj_t* a) {
     return KLB_OK;
 }
 
+// The TMA map of a state-shaped buffer (a checkpoint, a recomputed state, a
+// lambda) with the tile kernel's box of `rows` rows, encoded once per buffer.
+static const CUtensorMap* adj_map(klb_adj_t* a, const void* buf, int rows) {
+    for (const auto& m : a->maps)
+        if (m.buf == buf && m.rows == rows) return &m.map;
+    AdjMap m;
+    m.buf = buf;
+    m.rows = rows;
+    if (encode_state_map(a->h, buf, 48u, (unsigned)rows, 1u, &m.map) != KLB_OK) return nullptr;
+    a->maps.push_back(m);
+    return &a->maps.back().map;
+}
+
 // the node kernel: one CTA row per grid row, columns strided over 256 threads
 static dim3 node_grid(const Geom& g) { return dim3((unsigned)((g.nx + 255) / 256), (unsigned)g.ny); }
 
@@ -101,9 +122,13 @@ static int vjp_step(klb_adj_t* a, const void* f, void* lam_in, void* lam_out, do
     // sensitivities, then the fused faces-and-gather pass
     launch_fold<T>(g, (T*)lam_in, h->stream);
     adj_node_kernel<T><<<node_grid(g), 256, 0, h->stream>>>(c, g, (const T*)f, (const T*)lam_in, (T*)a->Nb);
-    const long long tiles = (long long)AdjTile<kAdjRows>::tiles_x(g.nx) * AdjTile<kAdjRows>::tiles_y(g.ny);
+    using A = AdjTile<T, kAdjRows>;
+    const CUtensorMap* fmap = adj_map(a, f, A::FR);
+    const CUtensorMap* lmap = adj_map(a, lam_in, A::LR);
+    if (!fmap || !lmap) return afail(a, KLB_E_CUDA, h->err);
+    const long long tiles = (long long)A::tiles_x(g.nx) * A::tiles_y(g.ny);
     adj_tile_kernel<T, kAdjRows><<<dim3((unsigned)tiles, NQ), 32 * kAdjRows, 0, h->stream>>>(
-        c, g, (const T*)f, (const T*)lam_in, (const T*)a->Nb, T(coef), (T*)lam_out);
+        *fmap, *lmap, c, g, (const T*)a->Nb, T(coef), (T*)lam_out, h->err_dev, h->spin_limit);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return afail(a, KLB_E_CUDA, std::string("adjoint kernels: ") + cudaGetErrorString(e));
     h->launches += 3;
@@ -386,9 +411,8 @@ int klb_adjoint_vjp(klb_adj_t* a, const double* lam_N, double* lam_0, int on_dev
     if (e != cudaSuccess) return afail(a, KLB_E_CUDA, cudaGetErrorString(e));
     ACK(a, cudaMemcpyAsync(lam_0, a->dense, sizeof(double) * NQ * nn,
                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
-    ACK(a, cudaStreamSynchronize(h->stream));
     a->forward_done = false;
-    return KLB_OK;
+    return klb_sync(h) == KLB_OK ? KLB_OK : afail(a, KLB_E_CUDA, h->err);  // also a bounded wait that ran out
 }
 
 int klb_adjoint_samples(klb_adj_t* a, double* out, int64_t cap, int64_t* count) {

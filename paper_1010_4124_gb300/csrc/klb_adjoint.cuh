@@ -18,6 +18,7 @@
 //     (d f^(0) / d(rho, u_x, u_y, T))^T lambda^0 for the initial fields.
 #pragma once
 #include "klb_device.cuh"
+#include "klb_launch.h"
 
 namespace fdlb {
 
@@ -321,96 +322,69 @@ __global__ void __launch_bounds__(256) adj_node_kernel(const StepConst<T> c, con
 
 // Tiles of the reverse step: 32 x TY positions of the extended grid (columns
 // -4 .. nx + 2, rows -3 .. ny + 2: interior nodes and the ghost positions
-// whose sums the node kernel folds back).  One CTA per (tile, velocity q).
-template <int TY>
+// whose sums the fold kernel adds back).  One CTA per (tile, velocity q).
+// Both staged boxes are BW = 48 positions wide and start 8 positions left of
+// the tile's lane 0 (array column 32 tx - 8: 16-byte aligned for TMA): the f
+// box holds rows -5 .. TY + 4 of the tile, the lambda box rows -3 .. TY + 2.
+template <typename T, int TY>
 struct AdjTile {
-    static constexpr int TX = 32;
+    static constexpr int TX = 32, BW = 48;
+    static constexpr int FR = TY + 10, LR = TY + 6;
     static __host__ __device__ int tiles_x(int nx) { return (nx + GX + 3 + TX - 1) / TX; }
     static __host__ __device__ int tiles_y(int ny) { return (ny + 2 * GY + TY - 1) / TY; }
+    static_assert((BW * sizeof(T)) % 16 == 0, "TMA box rows of 16-byte multiples");
+    static_assert((FR * BW * sizeof(T)) % 128 == 0 && (LR * BW * sizeof(T)) % 128 == 0, "boxes keep 128-byte alignment");
 };
 
-// One CTA: velocity q = blockIdx.y on tile blockIdx.x.  f^n_q is staged with
-// a halo of 5 positions (the stencils of the faces within 3 of the tile), and
-// lambda^{n+1}_q with a halo of 3 (the faces' mu); every face whose stencil
-// reaches the tile is evaluated once into shared memory (the 5 entries
-// mu dh/dF), and each position gathers the entries that touch it.  A face
-// outside the grid (i < 0 or i > nx, or a row outside it) has mu = 0, since
-// lambda is zero off the interior, so no face needs a validity test.
-// Threads map to faces in three fixed passes: x faces 0..31 of each row, y
-// faces 0..TY-1 of each column, then the remaining 5 y-face rows (warps
-// 0..4) and 5 x-face columns (warps 5.., 4 rows of 5 per warp).
-template <typename T, int TY>
-__global__ void __launch_bounds__(32 * TY) adj_tile_kernel(const StepConst<T> c, const Geom g, const T* __restrict__ f,
-                                                           const T* __restrict__ lam, const T* __restrict__ N, T coef,
-                                                           T* __restrict__ lam_out) {
-    constexpr int TX = AdjTile<TY>::TX;
-    static_assert(TY >= 7, "the remainder pass needs warps 0..4 and two more");
-    __shared__ T fs[TY + 10][TX + 10];  // positions (y0 - 5 + r, x0 - 5 + s)
-    __shared__ T ls[TY + 6][TX + 6];    // positions (y0 - 3 + r, x0 - 3 + s)
-    __shared__ T gx[5][TY][TX + 5];     // x face i = x0 - 2 + s of row y0 + r
-    __shared__ T gy[5][TY + 5][TX];     // y face j = y0 - 2 + s of column x0 + l
-    const int q = blockIdx.y;
-    const int tiles_x = AdjTile<TY>::tiles_x(g.nx);
-    const int by = (int)blockIdx.x / tiles_x;
-    const int x0 = ((int)blockIdx.x - by * tiles_x) * TX - GX;
-    const int y0 = by * TY - GY;
+// The faces and the gather of one CTA for a velocity whose components have
+// the signs SX, SY (compile time, so no branch on them remains): every face
+// whose stencil reaches the tile is evaluated once into shared memory (the
+// five entries mu dh/dF), and each position gathers the entries that touch
+// it.  A face outside the grid (i < 0 or i > nx, or a row outside it) has
+// mu = 0 since lambda is zero off the interior, so no face needs a validity
+// test.  Threads map to faces in three fixed passes: x faces 0..31 of each
+// row, y faces 0..TY-1 of each column, then the remaining 5 y-face rows
+// (warps 0..4) and 5 x-face columns (warps 5.., 4 rows of 5 per warp).
+template <typename T, int TY, int SX, int SY>
+__device__ __forceinline__ void adj_tile_body(const StepConst<T>& c, const Geom& g, int q, int x0, int y0,
+                                              const T (*fs)[AdjTile<T, TY>::BW], const T (*ls)[AdjTile<T, TY>::BW],
+                                              T (*gx)[TY][AdjTile<T, TY>::TX + 5], T (*gy)[TY + 5][AdjTile<T, TY>::TX],
+                                              const T* __restrict__ N, T coef, T* __restrict__ lam_out) {
+    constexpr int TX = AdjTile<T, TY>::TX;
     const int l = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const T* F = f + q * g.plane;
-    const T* L = lam + q * g.plane;
-    const T vx = c.vx[q], vy = c.vy[q];
-
-    for (int r = w; r < TY + 10; r += TY) {
-        const int y = y0 - 5 + r;
-        const bool yin = y >= -GY && y < g.ny + GY;
-        const T* row = F + (long long)(y + GY) * g.px + GX;
-        for (int s = l; s < TX + 10; s += 32) {
-            const int x = x0 - 5 + s;
-            fs[r][s] = (yin && x >= -GX && x < g.px - GX) ? row[x] : T(0);
-        }
-    }
-    for (int r = w; r < TY + 6; r += TY) {
-        const int y = y0 - 3 + r;
-        const bool yin = y >= 0 && y < g.ny;  // ghosts are not state variables
-        const T* row = L + (long long)(y + GY) * g.px + GX;
-        for (int s = l; s < TX + 6; s += 32) {
-            const int x = x0 - 3 + s;
-            ls[r][s] = (yin && x >= 0 && x < g.nx) ? row[x] : T(0);
-        }
-    }
-    __syncthreads();
-    const T e34 = T(0.75) * c.eps;
-    // x face s of row r: stencil fs[r + 5][s .. s + 5] (upwind order by the
-    // sign of v_x), mu from lambda at columns s + 1 (right) and s (left)
+    const T vx = c.vx[q], vy = c.vy[q], e34 = T(0.75) * c.eps;
+    // box columns: f position x0 - 8 + col, lambda the same; face s of a row
+    // lies between positions x0 - 3 + s and x0 - 2 + s (face i = x0 - 2 + s)
     auto face_x = [&](int r, int s) {
-        const T* row = &fs[r + 5][0];
+        const T* row = fs[r + 5];
         T gr[5];
-        if (vx > T(0))
-            weno5_grad(vx * row[s], vx * row[s + 1], vx * row[s + 2], vx * row[s + 3], vx * row[s + 4], e34, gr);
+        if (SX > 0)
+            weno5_grad(vx * row[s + 3], vx * row[s + 4], vx * row[s + 5], vx * row[s + 6], vx * row[s + 7], e34, gr);
         else
-            weno5_grad(vx * row[s + 5], vx * row[s + 4], vx * row[s + 3], vx * row[s + 2], vx * row[s + 1], e34, gr);
-        const T mu = c.cx[q] * (ls[r + 3][s + 1] - ls[r + 3][s]);  // dt v_x / dx times the jump of lambda
+            weno5_grad(vx * row[s + 8], vx * row[s + 7], vx * row[s + 6], vx * row[s + 5], vx * row[s + 4], e34, gr);
+        const T mu = c.cx[q] * (ls[r + 3][s + 6] - ls[r + 3][s + 5]);  // dt v_x / dx times the jump of lambda
 #pragma unroll
         for (int e = 0; e < 5; ++e) gx[e][r][s] = mu * gr[e];
     };
-    // y face s of column cl: stencil fs[s .. s + 5][cl + 5]
+    // y face s of column cl: between rows y0 - 3 + s and y0 - 2 + s
     auto face_y = [&](int s, int cl) {
+        const int x = cl + 8;
         T gr[5];
-        const int x = cl + 5;
-        if (vy > T(0))
+        if (SY > 0)
             weno5_grad(vy * fs[s][x], vy * fs[s + 1][x], vy * fs[s + 2][x], vy * fs[s + 3][x], vy * fs[s + 4][x], e34,
                        gr);
         else
             weno5_grad(vy * fs[s + 5][x], vy * fs[s + 4][x], vy * fs[s + 3][x], vy * fs[s + 2][x], vy * fs[s + 1][x],
                        e34, gr);
-        const T mu = c.cy[q] * (ls[s + 1][cl + 3] - ls[s][cl + 3]);
+        const T mu = c.cy[q] * (ls[s + 1][x] - ls[s][x]);
 #pragma unroll
         for (int e = 0; e < 5; ++e) gy[e][s][cl] = mu * gr[e];
     };
-    if (q > 0) {
+    if (SX != 0) {
         face_x(w, l);
-        if (vy != T(0)) face_y(w, l);
+        if (SY != 0) face_y(w, l);
         if (w < 5) {
-            if (vy != T(0)) face_y(TY + w, l);
+            if (SY != 0) face_y(TY + w, l);
         } else if (l < 20) {
             const int rr = 4 * (w - 5) + l / 5;
             if (rr < TY) face_x(rr, TX + l % 5);
@@ -423,29 +397,19 @@ __global__ void __launch_bounds__(32 * TY) adj_tile_kernel(const StepConst<T> c,
     const bool yg = (y >= -GY && y < 0) || (y >= g.ny && y < g.ny + 3);
     if (!((xin && yin) || (xg && yin) || (xin && yg))) return;
     T acc = T(0);
-    if (q > 0 && yin) {  // x faces whose stencil holds position x (its slot e in that stencil)
-        if (vx > T(0)) {
+    if (SX != 0 && yin) {  // x faces whose stencil holds position x (its slot e in that stencil)
 #pragma unroll
-            for (int e = 0; e < 5; ++e) acc += gx[e][w][l + 5 - e];
-        } else {
-#pragma unroll
-            for (int e = 0; e < 5; ++e) acc += gx[e][w][l + e];
-        }
+        for (int e = 0; e < 5; ++e) acc += gx[e][w][SX > 0 ? l + 5 - e : l + e];
     }
-    if (q > 0 && vy != T(0) && xin) {
-        if (vy > T(0)) {
+    if (SY != 0 && xin) {
 #pragma unroll
-            for (int e = 0; e < 5; ++e) acc += gy[e][w + 5 - e][l];
-        } else {
-#pragma unroll
-            for (int e = 0; e < 5; ++e) acc += gy[e][w + e][l];
-        }
+        for (int e = 0; e < 5; ++e) acc += gy[e][SY > 0 ? w + 5 - e : w + e][l];
     }
     const long long at = q * g.plane + (long long)(y + GY) * g.px + (x + GX);
     if (xin && yin) {
         const long long n = (long long)g.nx * g.ny, t = (long long)y * g.nx + x;
         const T gm0 = N[t], gm1 = N[n + t], gm2 = N[2 * n + t], gm3 = N[3 * n + t];
-        T v = (T(1) - c.relax) * ls[w + 3][l + 3] + c.relax * (gm0 + gm1 * vx + gm2 * vy + gm3 * T(0.5) * c.v2[q]);
+        T v = (T(1) - c.relax) * ls[w + 3][l + 8] + c.relax * (gm0 + gm1 * vx + gm2 * vy + gm3 * T(0.5) * c.v2[q]);
         if (coef != T(0)) {
             const T uy = N[4 * n + t];
             v += coef * (uy * vy - T(0.5) * uy * uy);
@@ -454,6 +418,61 @@ __global__ void __launch_bounds__(32 * TY) adj_tile_kernel(const StepConst<T> c,
     } else {
         lam_out[at] = acc;  // a ghost position: its sum waits for the fold
     }
+}
+
+// One CTA: velocity q = blockIdx.y on tile blockIdx.x.  f^n_q (halo 5: the
+// stencils of the faces within 3 of the tile) and lambda^{n+1}_q (halo 3: the
+// faces' mu) arrive by two TMA box loads (plain cp.async.bulk.tensor, no
+// multicast) on one mbarrier; a wait that runs out sets ERR_TIMEOUT.
+// lambda's cells off the interior are zero (ghosts cleared by the fold, pads
+// and corners never written), so the box needs no masking.
+template <typename T, int TY>
+__global__ void __launch_bounds__(32 * TY) adj_tile_kernel(const __grid_constant__ CUtensorMap fmap,
+                                                           const __grid_constant__ CUtensorMap lmap,
+                                                           const StepConst<T> c, const Geom g,
+                                                           const T* __restrict__ N, T coef, T* __restrict__ lam_out,
+                                                           int* __restrict__ err, long long spin_limit) {
+    using A = AdjTile<T, TY>;
+    constexpr int TX = A::TX;
+    static_assert(TY >= 7, "the remainder pass needs warps 0..4 and two more");
+    __shared__ __align__(128) T fs[A::FR][A::BW];
+    __shared__ __align__(128) T ls[A::LR][A::BW];
+    __shared__ T gx[5][TY][TX + 5];  // x face i = x0 - 2 + s of row y0 + r
+    __shared__ T gy[5][TY + 5][TX];  // y face j = y0 - 2 + s of column x0 + l
+    __shared__ __align__(8) uint64_t bar;
+    const int q = blockIdx.y;
+    const int tiles_x = A::tiles_x(g.nx);
+    const int by = (int)blockIdx.x / tiles_x, bx = (int)blockIdx.x - by * tiles_x;
+    const int x0 = bx * TX - GX, y0 = by * TY - GY;
+    const uint32_t b = smem_u32(&bar);
+    if (threadIdx.x == 0) {
+        mbar_init(b, 1);
+        fence_barrier_init();
+        fence_proxy_async();
+        mbar_arrive_expect_tx(b, (uint32_t)(sizeof(T) * A::BW * (A::FR + A::LR)));
+        tma_load_3d(smem_u32(&fs[0][0]), &fmap, bx * TX - 8, by * TY - 5, q, b);
+        tma_load_3d(smem_u32(&ls[0][0]), &lmap, bx * TX - 8, by * TY - 3, q, b);
+    }
+    __syncthreads();
+    const bool late = !mbar_wait_bounded(b, 0, spin_limit);
+    if (__syncthreads_or(late)) {
+        if (threadIdx.x == 0) {
+            atomicOr(err, ERR_TIMEOUT);
+            mbar_wait_bounded(b, 0, kDrainPolls);  // let the copies land before the CTA leaves
+        }
+        __syncthreads();
+        return;
+    }
+    const int sx = sgn_x(q), sy = sgn_y(q);  // uniform across the CTA
+#define KLB_ADJ_BODY(SX, SY) adj_tile_body<T, TY, SX, SY>(c, g, q, x0, y0, fs, ls, gx, gy, N, coef, lam_out)
+    if (sx == 0) KLB_ADJ_BODY(0, 0);
+    else if (sx > 0 && sy > 0) KLB_ADJ_BODY(1, 1);
+    else if (sx > 0 && sy < 0) KLB_ADJ_BODY(1, -1);
+    else if (sx > 0) KLB_ADJ_BODY(1, 0);
+    else if (sy > 0) KLB_ADJ_BODY(-1, 1);
+    else if (sy < 0) KLB_ADJ_BODY(-1, -1);
+    else KLB_ADJ_BODY(-1, 0);
+#undef KLB_ADJ_BODY
 }
 
 // lam := src[19][ny][nx] on the interior; the ghost cells stay zero (the

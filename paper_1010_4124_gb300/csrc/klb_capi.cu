@@ -144,33 +144,33 @@ static EncodeTiledFn encode_fn() {
     return fn;
 }
 
-// 3-D map over (x: pitch, y: ny + 6 rows, z: 19 planes) with the step's box.
-static int make_map(klb_t* h, void* base, CUtensorMap* map) {
+// 3-D map over (x: pitch, y: ny + 6 rows, z: 19 planes) of a state buffer of
+// the handle's layout, with the given box (x extent a 16-byte multiple).
+int fdlb::encode_state_map(klb_t* h, const void* base, unsigned bx, unsigned by, unsigned bz, CUtensorMap* map) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return fail(h, KLB_E_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
     const Geom& g = h->g;
     cuuint64_t dims[3] = {(cuuint64_t)g.px, (cuuint64_t)(g.ny + 2 * GY), (cuuint64_t)NQ};
     cuuint64_t strides[2] = {(cuuint64_t)g.px * h->esize, (cuuint64_t)g.plane * h->esize};
-    cuuint32_t box[3];
+    cuuint32_t box[3] = {bx, by, bz};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(map, h->p.precision == KLB_FP64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                    3, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(h, KLB_E_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+    return KLB_OK;
+}
+
+// the map of a state buffer with the step kernel's box
+static int make_map(klb_t* h, void* base, CUtensorMap* map) {
     if (h->p.precision == KLB_FP64) {  // one tile of TX x TY nodes plus halo
         int TX, TY;
         f64_tile(&TX, &TY);
-        box[0] = (cuuint32_t)(TX + 8);
-        box[1] = (cuuint32_t)(TY + 6);
-        box[2] = (cuuint32_t)NQ;
-    } else {  // one tile of the persistent FP32 kernel
-        unsigned bx, by, bz;
-        f32_box(h->variant, &bx, &by, &bz);
-        box[0] = bx;
-        box[1] = by;
-        box[2] = bz;
+        return fdlb::encode_state_map(h, base, (unsigned)(TX + 8), (unsigned)(TY + 6), (unsigned)NQ, map);
     }
-    cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = fn(map, h->p.precision == KLB_FP64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
-                    3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return fail(h, KLB_E_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
-    return KLB_OK;
+    unsigned bx, by, bz;  // one tile of the persistent FP32 kernel
+    f32_box(h->variant, &bx, &by, &bz);
+    return fdlb::encode_state_map(h, base, bx, by, bz, map);
 }
 
 extern "C" {

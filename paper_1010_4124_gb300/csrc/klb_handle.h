@@ -62,5 +62,8 @@ void step_constants(const klb_params& p, StepConst<double>& c);
 // helpers of klb_capi.cu used by the batch engine
 int handle_fail(klb_t* h, int code, const std::string& msg);
 int handle_upload_descs(klb_t* h);  // (re)build the FP32 descriptors and the tile count
+// TMA map of a state buffer of the handle's layout (x: pitch, y: rows with
+// ghosts, z: 19 planes) with a box of bx x by x bz elements
+int encode_state_map(klb_t* h, const void* base, unsigned bx, unsigned by, unsigned bz, CUtensorMap* map);
 void handle_after_step(klb_t* h);   // advance the step counter and the parity
 }  // namespace fdlb
