@@ -25,7 +25,7 @@ using namespace fdlb;
 
 struct AdjMap {  // a TMA map of one buffer for the tile kernel
     const void* buf = nullptr;
-    int rows = 0;
+    unsigned box[3] = {0, 0, 0};
     CUtensorMap map;
 };
 
@@ -85,20 +85,22 @@ static int raw_step(klb_adj_t* a) {
 }
 
 // The TMA map of a state-shaped buffer (a checkpoint, a recomputed state, a
-// lambda) with the tile kernel's box of `rows` rows, encoded once per buffer.
-static const CUtensorMap* adj_map(klb_adj_t* a, const void* buf, int rows) {
+// lambda) with a box of bx x by x bz elements, encoded once per buffer and box.
+static const CUtensorMap* adj_map(klb_adj_t* a, const void* buf, unsigned bx, unsigned by, unsigned bz) {
     for (const auto& m : a->maps)
-        if (m.buf == buf && m.rows == rows) return &m.map;
+        if (m.buf == buf && m.box[0] == bx && m.box[1] == by && m.box[2] == bz) return &m.map;
     AdjMap m;
     m.buf = buf;
-    m.rows = rows;
-    if (encode_state_map(a->h, buf, 48u, (unsigned)rows, 1u, &m.map) != KLB_OK) return nullptr;
+    m.box[0] = bx;
+    m.box[1] = by;
+    m.box[2] = bz;
+    if (encode_state_map(a->h, buf, bx, by, bz, &m.map) != KLB_OK) return nullptr;
     a->maps.push_back(m);
     return &a->maps.back().map;
 }
 
-// the node kernel: one CTA row per grid row, columns strided over 256 threads
-static dim3 node_grid(const Geom& g) { return dim3((unsigned)((g.nx + 255) / 256), (unsigned)g.ny); }
+// the node kernel: one CTA per segment of kNodeSeg nodes of each row
+static dim3 node_grid(const Geom& g) { return dim3((unsigned)((g.nx + kNodeSeg - 1) / kNodeSeg), (unsigned)g.ny); }
 
 // tile rows of the fused reverse step: 8 (its shared memory in FP64 stays
 // within the static 48 KB)
@@ -120,12 +122,15 @@ static int vjp_step(klb_adj_t* a, const void* f, void* lam_in, void* lam_out, do
     const Geom& g = h->g;
     // fold lambda^{n+1}'s ghost sums into its nodes, form the per-node f^(0)
     // sensitivities, then the fused faces-and-gather pass
-    launch_fold<T>(g, (T*)lam_in, h->stream);
-    adj_node_kernel<T><<<node_grid(g), 256, 0, h->stream>>>(c, g, (const T*)f, (const T*)lam_in, (T*)a->Nb);
     using A = AdjTile<T, kAdjRows>;
-    const CUtensorMap* fmap = adj_map(a, f, A::FR);
-    const CUtensorMap* lmap = adj_map(a, lam_in, A::LR);
-    if (!fmap || !lmap) return afail(a, KLB_E_CUDA, h->err);
+    const CUtensorMap* fmap = adj_map(a, f, A::BW, A::FR, 1);
+    const CUtensorMap* lmap = adj_map(a, lam_in, A::BW, A::LR, 1);
+    const CUtensorMap* fnode = adj_map(a, f, kNodeSeg, 1, NQ);
+    const CUtensorMap* lnode = adj_map(a, lam_in, kNodeSeg, 1, NQ);
+    if (!fmap || !lmap || !fnode || !lnode) return afail(a, KLB_E_CUDA, h->err);
+    launch_fold<T>(g, (T*)lam_in, h->stream);
+    adj_node_kernel<T><<<node_grid(g), kNodeSeg, 0, h->stream>>>(*fnode, *lnode, c, g, (T*)a->Nb, h->err_dev,
+                                                                 h->spin_limit);
     const long long tiles = (long long)A::tiles_x(g.nx) * A::tiles_y(g.ny);
     adj_tile_kernel<T, kAdjRows><<<dim3((unsigned)tiles, NQ), 32 * kAdjRows, 0, h->stream>>>(
         *fmap, *lmap, c, g, (const T*)a->Nb, T(coef), (T*)lam_out, h->err_dev, h->spin_limit);

@@ -294,30 +294,55 @@ __global__ void adj_fold_kernel(const Geom g, T* __restrict__ lam, int nbx, int 
     }
 }
 
-// Per interior node (row j = blockIdx.y, columns strided over the block), on
-// a folded lambda: the f^(0) sensitivity carried to the moments
-// (feq_vjp_moments, four values) and u_y into N[5][nx * ny].
+// Per interior node, on a folded lambda: the f^(0) sensitivity carried to
+// the moments (feq_vjp_moments, four values) and u_y into N[5][nx * ny].  One
+// CTA per segment of kNodeSeg nodes of row j = blockIdx.y: the segment's 19
+// planes of f and of lambda arrive by two TMA box loads (kNodeSeg x 1 x 19)
+// on a bounded mbarrier, so all 38 values of a node are fetched at once.
+constexpr int kNodeSeg = 128;
 template <typename T>
-__global__ void __launch_bounds__(256) adj_node_kernel(const StepConst<T> c, const Geom g, const T* __restrict__ f,
-                                                       const T* __restrict__ lam, T* __restrict__ N) {
-    const int j = blockIdx.y;
-    const long long n = (long long)g.nx * g.ny;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.nx; i += gridDim.x * blockDim.x) {
-        const long long at = (long long)(j + GY) * g.px + (i + GX);
-        T ll[NQ], fl[NQ];
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            ll[q] = lam[q * g.plane + at];
-            fl[q] = f[q * g.plane + at];
-        }
-        const Mom<T> m = moments_of(c, fl);
-        T gm[4];
-        feq_vjp_moments(c, m, ll, gm);
-        const long long t = (long long)j * g.nx + i;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) N[k * n + t] = gm[k];
-        N[4 * n + t] = m.uy;
+__global__ void __launch_bounds__(kNodeSeg) adj_node_kernel(const __grid_constant__ CUtensorMap fmap,
+                                                            const __grid_constant__ CUtensorMap lmap,
+                                                            const StepConst<T> c, const Geom g, T* __restrict__ N,
+                                                            int* __restrict__ err, long long spin_limit) {
+    __shared__ __align__(128) T fsm[NQ][kNodeSeg];
+    __shared__ __align__(128) T lsm[NQ][kNodeSeg];
+    __shared__ __align__(8) uint64_t bar;
+    const int j = blockIdx.y, i0 = blockIdx.x * kNodeSeg, tid = threadIdx.x;
+    const uint32_t b = smem_u32(&bar);
+    if (tid == 0) {
+        mbar_init(b, 1);
+        fence_barrier_init();
+        fence_proxy_async();
+        mbar_arrive_expect_tx(b, (uint32_t)(2 * sizeof(T) * NQ * kNodeSeg));
+        tma_load_3d(smem_u32(&fsm[0][0]), &fmap, i0 + GX, j + GY, 0, b);
+        tma_load_3d(smem_u32(&lsm[0][0]), &lmap, i0 + GX, j + GY, 0, b);
     }
+    __syncthreads();
+    const bool late = !mbar_wait_bounded(b, 0, spin_limit);
+    if (__syncthreads_or(late)) {
+        if (tid == 0) {
+            atomicOr(err, ERR_TIMEOUT);
+            mbar_wait_bounded(b, 0, kDrainPolls);  // let the copies land before the CTA leaves
+        }
+        __syncthreads();
+        return;
+    }
+    const int i = i0 + tid;
+    if (i >= g.nx) return;
+    T ll[NQ], fl[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        ll[q] = lsm[q][tid];
+        fl[q] = fsm[q][tid];
+    }
+    const Mom<T> m = moments_of(c, fl);
+    T gm[4];
+    feq_vjp_moments(c, m, ll, gm);
+    const long long n = (long long)g.nx * g.ny, t = (long long)j * g.nx + i;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) N[k * n + t] = gm[k];
+    N[4 * n + t] = m.uy;
 }
 
 // Tiles of the reverse step: 32 x TY positions of the extended grid (columns
