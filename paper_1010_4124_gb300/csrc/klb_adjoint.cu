@@ -40,7 +40,8 @@ struct klb_adj {
     void* Nb = nullptr;            // per-node f^(0) sensitivity and u_y (5 * nx * ny)
     double* fields = nullptr;      // the initial fields (4 * nx * ny)
     double* dense = nullptr;       // staging for host / dense arrays (19 * nx * ny)
-    std::deque<AdjMap> maps;       // the tile kernel's maps of the buffers above (stable addresses)
+    std::deque<AdjMap> maps;       // TMA maps of the buffers above (stable addresses)
+    InstDesc* rdescs = nullptr;    // FP32: step descriptors of the recomputation chains (device)
     std::vector<double> K;         // K_s of the forward run
     double ke = 0, gamma = 0;
     bool forward_done = false;
@@ -66,23 +67,6 @@ static int grid_of(long long n) {
 }
 
 static size_t state_bytes(const klb_t* h) { return (size_t)NQ * h->g.plane * h->esize; }
-
-// one raw step of the forward grid from buf[cur] into buf[1 - cur], no sampling
-static int raw_step(klb_adj_t* a) {
-    klb_t* h = a->h;
-    const int src = h->cur, dst = 1 - h->cur;
-    cudaError_t e;
-    if (h->p.precision == KLB_FP64)
-        e = launch_step<double>(h->map[src], h->cd, h->g, (double*)h->buf[dst], nullptr, h->err_dev, h->spin_limit,
-                                h->inject, h->stream);
-    else
-        e = launch_step_f32(h->cf, h->descs_dev + src, 1, h->ntiles, nullptr, h->err_dev, h->spin_limit, h->inject,
-                            h->variant, h->stream);
-    if (e != cudaSuccess) return afail(a, KLB_E_CUDA, std::string("step kernel: ") + cudaGetErrorString(e));
-    h->cur = dst;
-    h->launches += 1;
-    return KLB_OK;
-}
 
 // The TMA map of a state-shaped buffer (a checkpoint, a recomputed state, a
 // lambda) with a box of bx x by x bz elements, encoded once per buffer and box.
@@ -195,34 +179,80 @@ static double dL_dK(const klb_adj_t* a, int s, double g_ke, double g_gamma) {
     return d;
 }
 
+// One step of the recomputation from state buffer `in` into `out` (no
+// sampling).  FP32: the step kernel reads its input through a device
+// descriptor (TMA map of `in`, output pointer), one per (in, out) pair of the
+// sweep, uploaded once per reverse sweep (desc_index); FP64: the map of `in`.
+static int step_into(klb_adj_t* a, const void* in, void* out, int desc_index) {
+    klb_t* h = a->h;
+    cudaError_t e;
+    if (h->p.precision == KLB_FP64) {
+        int TX, TY;
+        f64_tile(&TX, &TY);
+        const CUtensorMap* m = adj_map(a, in, (unsigned)(TX + 8), (unsigned)(TY + 6), NQ);
+        if (!m) return afail(a, KLB_E_CUDA, h->err);
+        e = launch_step<double>(*m, h->cd, h->g, (double*)out, nullptr, h->err_dev, h->spin_limit, h->inject,
+                                h->stream);
+    } else {
+        e = launch_step_f32(h->cf, a->rdescs + desc_index, 1, h->ntiles, nullptr, h->err_dev, h->spin_limit,
+                            h->inject, h->variant, h->stream);
+    }
+    if (e != cudaSuccess) return afail(a, KLB_E_CUDA, std::string("step kernel: ") + cudaGetErrorString(e));
+    h->launches += 1;
+    return KLB_OK;
+}
+
+// FP32: the descriptors of the recomputation chains, for the grid's current
+// tile shape: entry s steps checkpoint s into seg[0], entry nck + k steps
+// seg[k] into seg[k + 1]
+static int upload_recompute_descs(klb_adj_t* a) {
+    klb_t* h = a->h;
+    if (h->p.precision != KLB_FP32 || a->seg.empty()) return KLB_OK;
+    unsigned bx, by, bz;
+    f32_box(h->variant, &bx, &by, &bz);
+    int tiles_x, ntiles;
+    f32_tiles(h->g.nx, h->g.ny, h->variant, &tiles_x, &ntiles);
+    std::vector<InstDesc> d(a->nck + a->seg.size() - 1);
+    for (size_t k = 0; k < d.size(); ++k) {
+        const void* in = k < (size_t)a->nck ? a->ck[k] : a->seg[k - a->nck];
+        void* out = k < (size_t)a->nck ? a->seg[0] : a->seg[k - a->nck + 1];
+        memset(&d[k], 0, sizeof(InstDesc));
+        if (encode_state_map(h, in, bx, by, bz, &d[k].map) != KLB_OK) return afail(a, KLB_E_CUDA, h->err);
+        d[k].out = (float*)out;
+        d[k].g = h->g;
+        d[k].tiles_x = tiles_x;
+        d[k].first_tile = 0;
+    }
+    ACK(a, cudaMemcpyAsync(a->rdescs, d.data(), d.size() * sizeof(InstDesc), cudaMemcpyHostToDevice, h->stream));
+    ACK(a, cudaStreamSynchronize(h->stream));  // the host vector goes out of scope
+    return KLB_OK;
+}
+
 // the reverse sweep from lam[cur_l] = lambda^N down to lambda^0; with
 // objective sources when `sources` is set (g_ke, g_gamma)
 static int reverse(klb_adj_t* a, bool sources, double g_ke, double g_gamma, int* lam_cur) {
-    klb_t* h = a->h;
     int lc = *lam_cur;
+    int r = upload_recompute_descs(a);
+    if (r != KLB_OK) return r;
     for (int s = a->nck - 1; s >= 0; --s) {
         fdlb::NvtxRange trace_("klb_adjoint segment");
         const int64_t n0 = (int64_t)s * a->ckpt;
         const int64_t n1 = std::min<int64_t>(n0 + a->ckpt, a->nsteps);
         const int len = (int)(n1 - n0);
-        // recompute the segment's states f^{n0} .. f^{n1-1} from its checkpoint
+        // recompute the segment's states f^{n0} .. f^{n1-1} from its checkpoint,
+        // straight into the segment buffers
         std::vector<const void*> states(len);
         states[0] = a->ck[s];
-        if (len > 1) {
-            ACK(a, cudaMemcpyAsync(h->buf[h->cur], a->ck[s], state_bytes(h), cudaMemcpyDeviceToDevice, h->stream));
-            for (int k = 1; k < len; ++k) {
-                int r = raw_step(a);
-                if (r != KLB_OK) return r;
-                ACK(a, cudaMemcpyAsync(a->seg[k - 1], h->buf[h->cur], state_bytes(h), cudaMemcpyDeviceToDevice,
-                                       h->stream));
-                states[k] = a->seg[k - 1];
-            }
+        for (int k = 1; k < len; ++k) {
+            r = step_into(a, states[k - 1], a->seg[k - 1], k == 1 ? s : a->nck + k - 2);
+            if (r != KLB_OK) return r;
+            states[k] = a->seg[k - 1];
         }
         for (int64_t n = n1 - 1; n >= n0; --n) {
             double coef = 0.0;
             const int si = sample_of(a, n);
             if (sources && si >= 0) coef = dL_dK(a, si, g_ke, g_gamma);
-            int r = vjp(a, states[n - n0], a->lam[lc], a->lam[1 - lc], coef);
+            r = vjp(a, states[n - n0], a->lam[lc], a->lam[1 - lc], coef);
             if (r != KLB_OK) return r;
             lc = 1 - lc;
         }
@@ -280,6 +310,7 @@ int klb_adjoint_create(const klb_params* p, int64_t nsteps, int32_t checkpoint_e
     for (size_t s = 0; s < a->seg.size() && ok; ++s) ok = cudaMalloc(&a->seg[s], sb) == cudaSuccess;
     for (int k = 0; k < 2 && ok; ++k) ok = cudaMalloc(&a->lam[k], sb) == cudaSuccess;
     ok = ok && cudaMalloc(&a->Nb, h->esize * 5 * nn) == cudaSuccess;
+    ok = ok && cudaMalloc(&a->rdescs, sizeof(InstDesc) * (a->nck + a->seg.size() + 1)) == cudaSuccess;
     ok = ok && cudaMalloc(&a->fields, sizeof(double) * 4 * nn) == cudaSuccess;
     ok = ok && cudaMalloc(&a->dense, sizeof(double) * NQ * nn) == cudaSuccess;
     if (!ok) {
@@ -302,6 +333,7 @@ void klb_adjoint_destroy(klb_adj_t* a) {
     for (int k = 0; k < 2; ++k)
         if (a->lam[k]) cudaFree(a->lam[k]);
     if (a->Nb) cudaFree(a->Nb);
+    if (a->rdescs) cudaFree(a->rdescs);
     if (a->fields) cudaFree(a->fields);
     if (a->dense) cudaFree(a->dense);
     klb_destroy(a->h);
