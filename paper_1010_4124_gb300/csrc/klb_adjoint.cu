@@ -112,22 +112,15 @@ static int vjp_step(klb_adj_t* a, const void* f, void* lam_in, void* lam_out, do
     const CUtensorMap* fnode = adj_map(a, f, kNodeSeg, 1, NQ);
     const CUtensorMap* lnode = adj_map(a, lam_in, kNodeSeg, 1, NQ);
     if (!fmap || !lmap || !fnode || !lnode) return afail(a, KLB_E_CUDA, h->err);
-    // grids of at least 6 x 6 nodes fold in the node kernel (one periodic
-    // image or three outflow ghosts per direction); smaller ones fold first
-    if (g.nx >= 6 && g.ny >= 6) {
-        adj_node_kernel<T, true><<<node_grid(g), kNodeSeg, 0, h->stream>>>(*fnode, *lnode, c, g, (T*)lam_in,
-                                                                           (T*)a->Nb, h->err_dev, h->spin_limit);
-    } else {
-        launch_fold<T>(g, (T*)lam_in, h->stream);
-        adj_node_kernel<T, false><<<node_grid(g), kNodeSeg, 0, h->stream>>>(*fnode, *lnode, c, g, (T*)lam_in,
-                                                                            (T*)a->Nb, h->err_dev, h->spin_limit);
-    }
+    launch_fold<T>(g, (T*)lam_in, h->stream);
+    adj_node_kernel<T><<<node_grid(g), kNodeSeg, 0, h->stream>>>(*fnode, *lnode, c, g, (T*)a->Nb, h->err_dev,
+                                                                 h->spin_limit);
     const long long tiles = (long long)A::tiles_x(g.nx) * A::tiles_y(g.ny);
     adj_tile_kernel<T, kAdjRows><<<dim3((unsigned)tiles, NQ), 32 * kAdjRows, 0, h->stream>>>(
         *fmap, *lmap, c, g, (const T*)a->Nb, T(coef), (T*)lam_out, h->err_dev, h->spin_limit);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return afail(a, KLB_E_CUDA, std::string("adjoint kernels: ") + cudaGetErrorString(e));
-    h->launches += (g.nx >= 6 && g.ny >= 6) ? 2 : 3;
+    h->launches += 3;
     return KLB_OK;
 }
 
@@ -409,8 +402,6 @@ int klb_adjoint_backward(klb_adj_t* a, double g_ke, double g_gamma, double* d_rh
     const int M = (int)a->K.size();
     int lc = 0;
     const double cN = dL_dK(a, M - 1, g_ke, g_gamma);
-    // lambda^N starts with clear ghost cells (a previous sweep leaves image sums there)
-    ACK(a, cudaMemsetAsync(a->lam[lc], 0, state_bytes(h), h->stream));
     int r = f64 ? source<double>(a, h->buf[h->cur], cN, a->lam[lc]) : source<float>(a, h->buf[h->cur], cN, a->lam[lc]);
     if (r != KLB_OK) return r;
     r = reverse(a, true, g_ke, g_gamma, &lc);

@@ -209,10 +209,10 @@ __device__ __forceinline__ int images(int i, int n, int per, int lo_out, int hi_
 //               + the objective's source at sampled steps.
 // A face's stencil may hold a ghost position, which is an image of an
 // interior node (periodic wrap or outflow copy, Eqs. 57, 63-64): the tile
-// kernel leaves those sums in the ghost cells of lambda^n, and the node
-// kernel of the next reverse step adds each ghost cell to the interior node
-// it images (grids under 6 nodes wide, and lambda^0 after the sweep: the
-// fold kernel, which also clears them).
+// kernel leaves those sums in the ghost cells of lambda^n, and the fold
+// kernel of the next reverse step (or after the last one) adds each ghost
+// cell to the interior node it images and clears it.  So lambda's ghost
+// cells are zero whenever a tile kernel reads them.
 // ---------------------------------------------------------------------------
 
 // Ghost cells that image interior node (i, j): along x (cells of the same
@@ -294,24 +294,17 @@ __global__ void adj_fold_kernel(const Geom g, T* __restrict__ lam, int nbx, int 
     }
 }
 
-// Per interior node: the f^(0) sensitivity carried to the moments
-// (feq_vjp_moments, four values) and u_y into N[5][nx * ny].  One CTA per
-// segment of kNodeSeg nodes of row j = blockIdx.y: the segment's 19 planes of
-// f and of lambda arrive by two TMA box loads (kNodeSeg x 1 x 19) on a
-// bounded mbarrier, so all 38 values of a node are fetched at once.  With
-// FOLD (grids of at least 6 x 6 nodes: at most one periodic image or three
-// outflow ghosts per direction), a node next to a periodic or outflow side
-// first adds the ghost-image sums of lambda (image_cells) and writes the
-// folded value back for the tile kernel; the ghost cells keep their sums,
-// which the tile kernel masks out and the next tile kernel overwrites.
-// Without FOLD lambda arrives folded (adj_fold_kernel).
+// Per interior node, on a folded lambda: the f^(0) sensitivity carried to
+// the moments (feq_vjp_moments, four values) and u_y into N[5][nx * ny].  One
+// CTA per segment of kNodeSeg nodes of row j = blockIdx.y: the segment's 19
+// planes of f and of lambda arrive by two TMA box loads (kNodeSeg x 1 x 19)
+// on a bounded mbarrier, so all 38 values of a node are fetched at once.
 constexpr int kNodeSeg = 128;
-template <typename T, bool FOLD>
+template <typename T>
 __global__ void __launch_bounds__(kNodeSeg) adj_node_kernel(const __grid_constant__ CUtensorMap fmap,
                                                             const __grid_constant__ CUtensorMap lmap,
-                                                            const StepConst<T> c, const Geom g, T* __restrict__ lam,
-                                                            T* __restrict__ N, int* __restrict__ err,
-                                                            long long spin_limit) {
+                                                            const StepConst<T> c, const Geom g, T* __restrict__ N,
+                                                            int* __restrict__ err, long long spin_limit) {
     __shared__ __align__(128) T fsm[NQ][kNodeSeg];
     __shared__ __align__(128) T lsm[NQ][kNodeSeg];
     __shared__ __align__(8) uint64_t bar;
@@ -337,24 +330,6 @@ __global__ void __launch_bounds__(kNodeSeg) adj_node_kernel(const __grid_constan
     }
     const int i = i0 + tid;
     if (i >= g.nx) return;
-    const long long at = (long long)(j + GY) * g.px + (i + GX);
-    if (FOLD && has_images(g, i, j)) {
-        long long cell[12];
-        const int m = image_cells(g, i, j, cell);  // at most 6 here
-        long long c6[6];
-#pragma unroll
-        for (int k = 0; k < 6; ++k) c6[k] = k < m ? cell[k] : 0;  // cell 0 of a plane: a corner pad, always zero
-#pragma unroll 4
-        for (int q = 0; q < NQ; ++q) {
-            const T* L = lam + q * g.plane;
-            T sum = T(0);
-#pragma unroll
-            for (int k = 0; k < 6; ++k) sum += L[c6[k]];
-            lsm[q][tid] += sum;
-        }
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) lam[q * g.plane + at] = lsm[q][tid];
-    }
     T ll[NQ], fl[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
@@ -474,8 +449,8 @@ __device__ __forceinline__ void adj_tile_body(const StepConst<T>& c, const Geom&
 // stencils of the faces within 3 of the tile) and lambda^{n+1}_q (halo 3: the
 // faces' mu) arrive by two TMA box loads (plain cp.async.bulk.tensor, no
 // multicast) on one mbarrier; a wait that runs out sets ERR_TIMEOUT.
-// lambda's cells off the interior are zero to the faces: tiles whose box
-// reaches past the interior clear those cells in shared memory.
+// lambda's cells off the interior are zero (ghosts cleared by the fold, pads
+// and corners never written), so the box needs no masking.
 template <typename T, int TY>
 __global__ void __launch_bounds__(32 * TY) adj_tile_kernel(const __grid_constant__ CUtensorMap fmap,
                                                            const __grid_constant__ CUtensorMap lmap,
@@ -512,16 +487,6 @@ __global__ void __launch_bounds__(32 * TY) adj_tile_kernel(const __grid_constant
         }
         __syncthreads();
         return;
-    }
-    // lambda is zero off the interior: a tile whose lambda box reaches past the
-    // interior clears those cells (ghost cells may hold image sums already folded)
-    if (x0 - 3 < 0 || x0 + TX + 3 > g.nx || y0 - 3 < 0 || y0 + TY + 3 > g.ny) {
-        for (int k = threadIdx.x; k < A::LR * A::BW; k += 32 * TY) {
-            const int r = k / A::BW, cc = k - r * A::BW;
-            const int y = y0 - 3 + r, x = x0 - 8 + cc;
-            if (!(y >= 0 && y < g.ny && x >= 0 && x < g.nx)) ls[r][cc] = T(0);
-        }
-        __syncthreads();
     }
     const int sx = sgn_x(q), sy = sgn_y(q);  // uniform across the CTA
 #define KLB_ADJ_BODY(SX, SY) adj_tile_body<T, TY, SX, SY>(c, g, q, x0, y0, fs, ls, gx, gy, N, coef, lam_out)
