@@ -49,6 +49,8 @@ extern "C" {
 #define KLB_E_DEVICE_TIMEOUT (-5) /* a bounded device-side wait ran out */
 #define KLB_E_STATE (-6)          /* call out of order (e.g. step before init) */
 #define KLB_E_IO (-7)             /* file I/O failed (save / load) */
+#define KLB_E_BOUNDS (-8)         /* bounds-checked build (libklb_checked.so) only: a kernel formed
+                                   * an index outside its buffer; the access was skipped */
 
 typedef enum { KLB_BC_PERIODIC = 0, KLB_BC_OUTFLOW = 1, KLB_BC_FIXED_EQ = 2 } klb_bc;
 typedef enum { KLB_FP32 = 0, KLB_FP64 = 1 } klb_prec;
@@ -196,6 +198,17 @@ int64_t klb_launch_count(const klb_t* h);
  * should be destroyed. */
 int klb_set_variant(klb_t* h, int variant);
 int klb_get_variant(const klb_t* h);
+
+/* Self-test of the bounds-checked debug build (libklb_checked.so, compiled
+ * with -DKLB_CHECK_BOUNDS, in which every kernel compares each global index it
+ * forms with the extent of its buffer, skips an access out of range and
+ * raises a flag that klb_sync reports as KLB_E_BOUNDS; nothing traps):
+ * enqueues one guarded store one element past the end of the handle's FP32
+ * state buffer, which the guard skips and flags, so that the next klb_sync
+ * returns KLB_E_BOUNDS (and clears the flag).  The ordinary library has no
+ * guards and refuses the call (KLB_E_INVAL) without launching anything.
+ * This is a debugging aid with no counterpart in the paper. */
+int klb_debug_bounds_probe(klb_t* h);
 
 /* ---------------------------------------------------------------------------
  * Batched engine (the D_v x D_rho sweeps of Sec. IV).  A batch holds n FP32

@@ -23,6 +23,10 @@
 
 using namespace fdlb;
 
+namespace fdlb {
+KLB_BOUNDS_QUERY(bounds_flag_adjoint)
+}  // namespace fdlb
+
 struct AdjMap {  // a TMA map of one buffer for the tile kernel
     const void* buf = nullptr;
     unsigned box[3] = {0, 0, 0};

@@ -287,10 +287,13 @@ __global__ void adj_fold_kernel(const Geom g, T* __restrict__ lam, int nbx, int 
         long long cell[12];
         const int m = image_cells(g, i, j, cell);
         const long long at = (long long)(j + GY) * g.px + (i + GX);
-        T v = L[at];
-        for (int k = 0; k < m; ++k) v += L[cell[k]];
-        for (int k = 0; k < m; ++k) L[cell[k]] = T(0);
-        L[at] = v;
+        const long long lim = (NQ - q) * g.plane;  // the cells of planes q .. 18 from L
+        T v = KLB_LOAD(L, at, lim, T(0));
+        for (int k = 0; k < m; ++k) v += KLB_LOAD(L, cell[k], lim, T(0));
+        for (int k = 0; k < m; ++k) {
+            KLB_GUARD(cell[k], lim) L[cell[k]] = T(0);
+        }
+        KLB_GUARD(at, lim) L[at] = v;
     }
 }
 
@@ -341,8 +344,10 @@ __global__ void __launch_bounds__(kNodeSeg) adj_node_kernel(const __grid_constan
     feq_vjp_moments(c, m, ll, gm);
     const long long n = (long long)g.nx * g.ny, t = (long long)j * g.nx + i;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) N[k * n + t] = gm[k];
-    N[4 * n + t] = m.uy;
+    for (int k = 0; k < 4; ++k) {
+        KLB_GUARD(k * n + t, 5 * n) N[k * n + t] = gm[k];
+    }
+    KLB_GUARD(4 * n + t, 5 * n) N[4 * n + t] = m.uy;
 }
 
 // Tiles of the reverse step: 32 x TY positions of the extended grid (columns
@@ -433,15 +438,16 @@ __device__ __forceinline__ void adj_tile_body(const StepConst<T>& c, const Geom&
     const long long at = q * g.plane + (long long)(y + GY) * g.px + (x + GX);
     if (xin && yin) {
         const long long n = (long long)g.nx * g.ny, t = (long long)y * g.nx + x;
-        const T gm0 = N[t], gm1 = N[n + t], gm2 = N[2 * n + t], gm3 = N[3 * n + t];
+        const T gm0 = KLB_LOAD(N, t, 5 * n, T(0)), gm1 = KLB_LOAD(N, n + t, 5 * n, T(0));
+        const T gm2 = KLB_LOAD(N, 2 * n + t, 5 * n, T(0)), gm3 = KLB_LOAD(N, 3 * n + t, 5 * n, T(0));
         T v = (T(1) - c.relax) * ls[w + 3][l + 8] + c.relax * (gm0 + gm1 * vx + gm2 * vy + gm3 * T(0.5) * c.v2[q]);
         if (coef != T(0)) {
-            const T uy = N[4 * n + t];
+            const T uy = KLB_LOAD(N, 4 * n + t, 5 * n, T(0));
             v += coef * (uy * vy - T(0.5) * uy * uy);
         }
-        lam_out[at] = v + acc;
+        KLB_GUARD(at, NQ * g.plane) lam_out[at] = v + acc;
     } else {
-        lam_out[at] = acc;  // a ghost position: its sum waits for the fold
+        KLB_GUARD(at, NQ * g.plane) lam_out[at] = acc;  // a ghost position: its sum waits for the fold
     }
 }
 
@@ -510,7 +516,8 @@ __global__ void adj_import_kernel(const Geom g, const double* __restrict__ src, 
         const int q = (int)(t / n);
         const long long r = t - q * n;
         const int i = (int)(r % g.nx), j = (int)(r / g.nx);
-        lam[q * g.plane + (long long)(j + GY) * g.px + (i + GX)] = T(src[t]);
+        const long long at = q * g.plane + (long long)(j + GY) * g.px + (i + GX);
+        KLB_GUARD(at, NQ * g.plane) lam[at] = T(KLB_LOAD(src, t, NQ * n, 0.0));
     }
 }
 
@@ -524,10 +531,12 @@ __global__ void adj_source_kernel(const StepConst<T> c, const Geom g, const T* _
         const long long at = (long long)(j + GY) * g.px + (i + GX);
         T fl[NQ];
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) fl[q] = f[q * g.plane + at];
+        for (int q = 0; q < NQ; ++q) fl[q] = KLB_LOAD(f, q * g.plane + at, NQ * g.plane, T(0));
         const Mom<T> m = moments_of(c, fl);
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) lam[q * g.plane + at] = coef * (m.uy * c.vy[q] - T(0.5) * m.uy * m.uy);
+        for (int q = 0; q < NQ; ++q) {
+            KLB_GUARD(q * g.plane + at, NQ * g.plane) lam[q * g.plane + at] = coef * (m.uy * c.vy[q] - T(0.5) * m.uy * m.uy);
+        }
     }
 }
 
@@ -543,7 +552,7 @@ __global__ void adj_fields_kernel(const StepConst<T> c, const Geom g, const doub
         const long long at = (long long)(j + GY) * g.px + (i + GX);
         T ll[NQ];
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) ll[q] = lam[q * g.plane + at];
+        for (int q = 0; q < NQ; ++q) ll[q] = KLB_LOAD(lam, q * g.plane + at, NQ * g.plane, T(0));
         T G[4];
         feq_vjp_fields(c, T(rho[t]), T(ux[t]), T(uy[t]), T(Tm[t]), ll, G);
         d_rho[t] = G[0];

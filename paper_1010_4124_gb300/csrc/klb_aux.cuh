@@ -61,8 +61,8 @@ __global__ void fixed_ghosts_kernel(const StepConst<T> c, const Geom g, const do
                 else if (side == 1) off = (long long)(iy + GY) * g.px + (g.nx - 1 + GX + d);
                 else if (side == 2) off = (long long)(GY - d) * g.px + (ix + GX);
                 else off = (long long)(g.ny - 1 + GY + d) * g.px + (ix + GX);
-                a[q * g.plane + off] = v;
-                b[q * g.plane + off] = v;
+                KLB_GUARD(q * g.plane + off, NQ * g.plane) a[q * g.plane + off] = v;
+                KLB_GUARD(q * g.plane + off, NQ * g.plane) b[q * g.plane + off] = v;
             }
         }
     }
@@ -75,7 +75,7 @@ __global__ void set_f_kernel(const Geom g, const double* __restrict__ src, T* __
          k += (long long)gridDim.x * blockDim.x) {
         const int q = (int)(k / n);
         const long long r = k % n;
-        store_with_images(dst, g, q, (int)(r % g.nx), (int)(r / g.nx), T(src[k]));
+        store_with_images(dst, g, q, (int)(r % g.nx), (int)(r / g.nx), T(KLB_LOAD(src, k, NQ * n, 0.0)));
     }
 }
 
@@ -87,7 +87,8 @@ __global__ void get_f_kernel(const Geom g, const T* __restrict__ src, double* __
         const int q = (int)(k / n);
         const long long r = k % n;
         const int ix = (int)(r % g.nx), iy = (int)(r / g.nx);
-        dst[k] = double(src[q * g.plane + (long long)(iy + GY) * g.px + (ix + GX)]);
+        const long long at = q * g.plane + (long long)(iy + GY) * g.px + (ix + GX);
+        KLB_GUARD(k, NQ * n) dst[k] = double(KLB_LOAD(src, at, NQ * g.plane, T(0)));
     }
 }
 
@@ -101,7 +102,8 @@ __global__ void fields_kernel(const StepConst<T> c, const Geom g, const T* __res
         const int ix = (int)(k % g.nx), iy = (int)(k / g.nx);
         T fl[NQ];
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) fl[q] = f[q * g.plane + (long long)(iy + GY) * g.px + (ix + GX)];
+        for (int q = 0; q < NQ; ++q)
+            fl[q] = KLB_LOAD(f, q * g.plane + (long long)(iy + GY) * g.px + (ix + GX), NQ * g.plane, T(0));
         const NodeEq<T> s = Arith<T>::node_state(c, fl);
         if (rho) rho[k] = s.rho;
         if (ux) ux[k] = s.ux;
@@ -121,7 +123,8 @@ __global__ void __launch_bounds__(TX* TY) diag_partials_kernel(const StepConst<T
     const bool active = ix < g.nx && iy < g.ny;
     T fl[NQ];
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) fl[q] = active ? f[q * g.plane + (long long)(iy + GY) * g.px + (ix + GX)] : T(1);
+    for (int q = 0; q < NQ; ++q)
+        fl[q] = active ? KLB_LOAD(f, q * g.plane + (long long)(iy + GY) * g.px + (ix + GX), NQ * g.plane, T(1)) : T(1);
     const NodeEq<T> s = Arith<T>::node_state(c, fl);
     double v[8];
     node_diag(s, active, v);
@@ -141,7 +144,8 @@ __global__ void __launch_bounds__(256) mean_density_kernel(const Geom g, const T
     for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
         double r = 0.0;
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) r += (double)row[q * g.plane + i];
+        for (int q = 0; q < NQ; ++q)
+            r += (double)KLB_LOAD(row, q * g.plane + i, NQ * g.plane - ((long long)(j + GY) * g.px + GX), T(0));
         s += r;
     }
 #pragma unroll
@@ -151,7 +155,7 @@ __global__ void __launch_bounds__(256) mean_density_kernel(const Geom g, const T
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
-        out[j] = t / g.nx;
+        KLB_GUARD(j, g.ny) out[j] = t / g.nx;
     }
 }
 

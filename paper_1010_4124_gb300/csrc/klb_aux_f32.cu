@@ -36,8 +36,10 @@ __device__ __forceinline__ void fold_records(const double* __restrict__ partials
     }
     if (threadIdx.x == 0) {
         const long long n = *counter;
-        double* out = ring + 7 * (n % cap);
-        for (int k = 0; k < 7; ++k) out[k] = red[0][k];
+        const long long slot = 7 * (n % cap);
+        for (int k = 0; k < 7; ++k) {
+            KLB_GUARD(slot + k, 7ll * cap) ring[slot + k] = red[0][k];
+        }
         *counter = n + 1;
         if (red[0][7] != 0.0) atomicOr(err, ERR_NONFINITE);
     }
@@ -61,6 +63,28 @@ cudaError_t launch_diag_finalize_batch(const DiagJob* jobs, int njobs, DueMask d
     if (njobs < 1) return cudaSuccess;
     diag_finalize_batch_kernel<<<njobs, 256, 0, s>>>(jobs, due);
     return cudaGetLastError();
+}
+
+KLB_BOUNDS_QUERY(bounds_flag_aux_f32)
+
+#ifdef KLB_CHECK_BOUNDS
+// self-test of the bounds-checked build: a store one element past the end of
+// a buffer of n elements, which the guard skips and flags
+__global__ void bounds_probe_kernel(float* p, long long n) {
+    KLB_GUARD(n, n) p[n] = 0.f;
+}
+#endif
+
+cudaError_t launch_bounds_probe(float* p, long long n, cudaStream_t s) {
+#ifdef KLB_CHECK_BOUNDS
+    bounds_probe_kernel<<<1, 1, 0, s>>>(p, n);
+    return cudaGetLastError();
+#else
+    (void)p;
+    (void)n;
+    (void)s;
+    return cudaErrorNotSupported;  // ordinary builds have no guard: never launched
+#endif
 }
 
 cudaError_t launch_diag_finalize(const double* partials, int nparts, double* ring, int cap, long long* counter,

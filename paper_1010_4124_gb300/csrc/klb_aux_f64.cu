@@ -13,4 +13,6 @@ cudaError_t launch_diag_partials<double>(const StepConst<double>& c, const Geom&
     return launch_diag_partials_tiles<double, 32, 8>(c, g, f, partials, s);
 }
 
+KLB_BOUNDS_QUERY(bounds_flag_aux_f64)
+
 }  // namespace fdlb

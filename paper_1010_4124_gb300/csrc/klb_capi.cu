@@ -21,6 +21,16 @@ static int fail(klb_t* h, int code, const std::string& msg) {
     return code;
 }
 int fdlb::handle_fail(klb_t* h, int code, const std::string& msg) { return fail(h, code, msg); }
+
+int fdlb::bounds_flags() {
+#ifdef KLB_CHECK_BOUNDS
+    return bounds_flag_aux_f32() | bounds_flag_aux_f64() | bounds_flag_step_f32() | bounds_flag_step_f32_lo() |
+           bounds_flag_step_f64() | bounds_flag_adjoint();
+#else
+    return 0;
+#endif
+}
+
 static int cuda_fail(klb_t* h, cudaError_t e, const char* where) {
     return fail(h, KLB_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
@@ -407,6 +417,8 @@ static int check_err(klb_t* h) {
     int v = 0;
     CK(h, cudaMemcpyAsync(&v, h->err_dev, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
+    if (fdlb::bounds_flags() != 0)
+        return fail(h, KLB_E_BOUNDS, "bounds-checked build: a kernel formed an index outside its buffer");
     if (v) {
         CK(h, cudaMemsetAsync(h->err_dev, 0, sizeof(int), h->stream));
         CK(h, cudaStreamSynchronize(h->stream));
@@ -611,6 +623,18 @@ int klb_debug_inject_wait_timeout(klb_t* h, int64_t polls) {
     h->inject = polls > 0 ? 1 : 0;
     h->spin_limit = polls > 0 ? polls : kDefaultSpin;
     return KLB_OK;
+}
+
+int klb_debug_bounds_probe(klb_t* h) {
+    if (!h) return KLB_E_INVAL;
+#ifdef KLB_CHECK_BOUNDS
+    if (h->p.precision != KLB_FP32) return fail(h, KLB_E_INVAL, "the probe writes past an FP32 state buffer");
+    cudaError_t e = launch_bounds_probe((float*)h->buf[h->cur], (long long)NQ * h->g.plane, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "bounds probe");
+    return KLB_OK;
+#else
+    return fail(h, KLB_E_INVAL, "the bounds probe exists in the bounds-checked build (libklb_checked.so) only");
+#endif
 }
 
 int klb_set_variant(klb_t* h, int variant) {

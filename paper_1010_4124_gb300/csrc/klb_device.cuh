@@ -20,6 +20,38 @@ constexpr int GY = 3;  // interior node (*, 0) sits at row GY (3 ghost rows)
 constexpr int ERR_TIMEOUT = 1;
 constexpr int ERR_NONFINITE = 2;
 
+// Bounds-checked builds (-DKLB_CHECK_BOUNDS, the debug library
+// libklb_checked.so): every global index a kernel forms into a state buffer,
+// a dense field array or a diagnostics ring is compared with the extent of
+// that buffer before the access.  An index out of range raises this
+// translation unit's flag and the access is skipped (a load then reads
+// zero); nothing traps, so the context stays usable and klb_sync reports
+// KLB_E_BOUNDS.  Without the macro the guards expand to nothing and the
+// accesses are exactly the unguarded ones.
+#ifdef KLB_CHECK_BOUNDS
+static __device__ int g_bounds_flag;
+__device__ __forceinline__ bool idx_ok(long long i, long long n) {
+    if (i >= 0 && i < n) return true;
+    atomicOr(&g_bounds_flag, 1);
+    return false;
+}
+#define KLB_GUARD(i, n) if (::fdlb::idx_ok((long long)(i), (long long)(n)))
+#define KLB_LOAD(p, i, n, zero) (::fdlb::idx_ok((long long)(i), (long long)(n)) ? (p)[(i)] : (zero))
+// host query of this translation unit's flag (read and cleared)
+#define KLB_BOUNDS_QUERY(name)                                              \
+    int name() {                                                            \
+        int v = 0, z = 0;                                                   \
+        if (cudaMemcpyFromSymbol(&v, g_bounds_flag, sizeof(int)) != cudaSuccess) return -1; \
+        if (v) cudaMemcpyToSymbol(g_bounds_flag, &z, sizeof(int));          \
+        return v;                                                           \
+    }
+#else
+#define KLB_GUARD(i, n)
+#define KLB_LOAD(p, i, n, zero) ((p)[(i)])
+#define KLB_BOUNDS_QUERY(name) \
+    int name() { return 0; }
+#endif
+
 // Direction i = 1..6 of a ring sits at 60 i degrees (Eq. 5, N = 6).  The sign
 // of each Cartesian component is fixed by the direction alone, so the upwind
 // side of every face is known at compile time.
@@ -399,13 +431,19 @@ __device__ __forceinline__ void write_images(T* __restrict__ out, const Geom& g,
 template <typename T>
 __device__ __forceinline__ void store_with_images(T* __restrict__ out, const Geom& g, int q, int ix, int iy,
                                                   T val) {
-    out[(long long)q * g.plane + (long long)(iy + GY) * g.px + (ix + GX)] = val;
+    const long long at = (long long)q * g.plane + (long long)(iy + GY) * g.px + (ix + GX);
+    KLB_GUARD(at, NQ * g.plane) out[at] = val;
     write_images(out, g, q, ix, iy, val);
 }
 
 template <typename T>
 __device__ __forceinline__ void write_images(T* __restrict__ out, const Geom& g, int q, int ix, int iy, T val) {
     const long long base = (long long)q * g.plane;
+    // the value at array cell (row, column) of plane q
+    auto put = [&](int row, int col) {
+        const long long at = base + (long long)row * g.px + col;
+        KLB_GUARD(at, NQ * g.plane) out[at] = val;
+    };
     // x ghost images (interior rows only)
     const bool xper = g.bcx_lo == 0;
     if (xper) {
@@ -414,20 +452,19 @@ __device__ __forceinline__ void write_images(T* __restrict__ out, const Geom& g,
             for (int m = -3; m <= 3; ++m) {
                 if (m == 0) continue;
                 int gxi = ix + m * g.nx;
-                if ((gxi >= -3 && gxi < 0) || (gxi >= g.nx && gxi < g.nx + 3))
-                    out[base + (long long)(iy + GY) * g.px + (gxi + GX)] = val;
+                if ((gxi >= -3 && gxi < 0) || (gxi >= g.nx && gxi < g.nx + 3)) put(iy + GY, gxi + GX);
             }
         }
     } else {
         if (ix == 0 && g.bcx_lo == 1) {
-            out[base + (long long)(iy + GY) * g.px + (GX - 1)] = val;
-            out[base + (long long)(iy + GY) * g.px + (GX - 2)] = val;
-            out[base + (long long)(iy + GY) * g.px + (GX - 3)] = val;
+            put(iy + GY, GX - 1);
+            put(iy + GY, GX - 2);
+            put(iy + GY, GX - 3);
         }
         if (ix == g.nx - 1 && g.bcx_hi == 1) {
-            out[base + (long long)(iy + GY) * g.px + (g.nx + GX)] = val;
-            out[base + (long long)(iy + GY) * g.px + (g.nx + GX + 1)] = val;
-            out[base + (long long)(iy + GY) * g.px + (g.nx + GX + 2)] = val;
+            put(iy + GY, g.nx + GX);
+            put(iy + GY, g.nx + GX + 1);
+            put(iy + GY, g.nx + GX + 2);
         }
     }
     // y ghost images (interior columns only)
@@ -438,20 +475,19 @@ __device__ __forceinline__ void write_images(T* __restrict__ out, const Geom& g,
             for (int m = -3; m <= 3; ++m) {
                 if (m == 0) continue;
                 int gyi = iy + m * g.ny;
-                if ((gyi >= -3 && gyi < 0) || (gyi >= g.ny && gyi < g.ny + 3))
-                    out[base + (long long)(gyi + GY) * g.px + (ix + GX)] = val;
+                if ((gyi >= -3 && gyi < 0) || (gyi >= g.ny && gyi < g.ny + 3)) put(gyi + GY, ix + GX);
             }
         }
     } else {
         if (iy == 0 && g.bcy_lo == 1) {
-            out[base + (long long)(GY - 1) * g.px + (ix + GX)] = val;
-            out[base + (long long)(GY - 2) * g.px + (ix + GX)] = val;
-            out[base + (long long)(GY - 3) * g.px + (ix + GX)] = val;
+            put(GY - 1, ix + GX);
+            put(GY - 2, ix + GX);
+            put(GY - 3, ix + GX);
         }
         if (iy == g.ny - 1 && g.bcy_hi == 1) {
-            out[base + (long long)(g.ny + GY) * g.px + (ix + GX)] = val;
-            out[base + (long long)(g.ny + GY + 1) * g.px + (ix + GX)] = val;
-            out[base + (long long)(g.ny + GY + 2) * g.px + (ix + GX)] = val;
+            put(g.ny + GY, ix + GX);
+            put(g.ny + GY + 1, ix + GX);
+            put(g.ny + GY + 2, ix + GX);
         }
     }
 }

@@ -114,4 +114,17 @@ cudaError_t launch_diag_partials(const StepConst<T>& c, const Geom& g, const T* 
 cudaError_t launch_diag_finalize(const double* partials, int nparts, double* ring, int cap, long long* counter,
                                  int* err, cudaStream_t s);
 
+// Bounds-checked builds: each translation unit's flag of an index out of
+// range (read and cleared; always 0 in ordinary builds), and their union.
+int bounds_flag_aux_f32();
+int bounds_flag_aux_f64();
+int bounds_flag_step_f32();
+int bounds_flag_step_f32_lo();
+int bounds_flag_step_f64();
+int bounds_flag_adjoint();
+int bounds_flags();
+// bounds-checked builds only: one guarded store past the end of a buffer of
+// n floats (skipped and flagged); cudaErrorNotSupported elsewhere
+cudaError_t launch_bounds_probe(float* p, long long n, cudaStream_t s);
+
 }  // namespace fdlb

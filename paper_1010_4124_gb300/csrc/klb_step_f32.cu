@@ -97,4 +97,6 @@ cudaError_t launch_diag_f32(const StepConst<float>& c, const Geom& g, const floa
     return cudaGetLastError();
 }
 
+KLB_BOUNDS_QUERY(bounds_flag_step_f32)
+
 }  // namespace fdlb

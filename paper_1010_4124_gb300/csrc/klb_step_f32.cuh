@@ -397,9 +397,12 @@ __global__ void __launch_bounds__(32 * TY, 16 / TY) step_f32_kernel(const __grid
             if (sgn_y(q) != 0) f[q] = fmaf(-c.cy[q], yf[(yslot(q) * (TY + 1) + ty + 1) * 32 + lane], f[q]);
         }
         if (active) {
-            float* o = out + (long long)(iy + GY) * g.px + (ix + GX);
+            const long long at = (long long)(iy + GY) * g.px + (ix + GX);
+            float* o = out + at;
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) __stwb(o + q * g.plane, f[q]);  // global store
+            for (int q = 0; q < NQ; ++q) {
+                KLB_GUARD(at + q * g.plane, NQ * g.plane) __stwb(o + q * g.plane, f[q]);  // global store
+            }
             if (has_images(g, ix, iy)) {
 #pragma unroll
                 for (int q = 0; q < NQ; ++q) write_images(out, g, q, ix, iy, f[q]);
@@ -430,7 +433,7 @@ __device__ __forceinline__ void diag_cta(const StepConst<float>& c, const Geom& 
         const bool active = ix >= 0 && ix < g.nx && iy < g.ny;
 #pragma unroll
         for (int q = 0; q < NQ; ++q)
-            fl[q] = active ? f[q * g.plane + (long long)(iy + GY) * g.px + (ix + GX)] : 1.f;
+            fl[q] = active ? KLB_LOAD(f, q * g.plane + (long long)(iy + GY) * g.px + (ix + GX), NQ * g.plane, 1.f) : 1.f;
         return active;
     };
     DiagAccF32 acc;

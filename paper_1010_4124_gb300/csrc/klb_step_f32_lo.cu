@@ -27,4 +27,6 @@ cudaError_t launch_step_f32_lo(const StepConst<float>& c, const InstDesc* descs,
     return launch_rows<16>(c, descs, ninst, ntiles, diag_partials, err, spin_limit, inject, grid, stream);
 }
 
+KLB_BOUNDS_QUERY(bounds_flag_step_f32_lo)
+
 }  // namespace fdlb

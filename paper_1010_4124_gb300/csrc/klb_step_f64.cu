@@ -14,4 +14,6 @@ void f64_tile(int* tx, int* ty) {
     *tx = StepTile<double>::TX;
     *ty = StepTile<double>::TY;
 }
+KLB_BOUNDS_QUERY(bounds_flag_step_f64)
+
 }  // namespace fdlb

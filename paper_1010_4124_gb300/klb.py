@@ -5,7 +5,8 @@ CUDA kernels.  Arrays may be numpy float64 arrays (host memory) or torch
 float64 CUDA tensors (device memory, passed by pointer with on_device = 1).
 The library must have been built (paper_1010_4124_gb300/build.py, or
 __graft_entry__.build()); loading fails loudly otherwise -- there is no CPU
-fallback.
+fallback.  With the environment variable KLB_CHECKED=1 the binding loads the
+bounds-checked debug build libklb_checked.so instead (built on first use).
 """
 from __future__ import annotations
 
@@ -16,10 +17,11 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libklb.so")
+LIB_CHECKED_PATH = os.path.join(HERE, "libklb_checked.so")
 
 KLB_OK = 0
 ERRORS = {-1: "KLB_E_INVAL", -2: "KLB_E_NOMEM", -3: "KLB_E_CUDA", -4: "KLB_E_NONFINITE",
-          -5: "KLB_E_DEVICE_TIMEOUT", -6: "KLB_E_STATE", -7: "KLB_E_IO"}
+          -5: "KLB_E_DEVICE_TIMEOUT", -6: "KLB_E_STATE", -7: "KLB_E_IO", -8: "KLB_E_BOUNDS"}
 BC = {"periodic": 0, "outflow": 1, "fixed_eq": 2}
 SCHEMES = {"weno5": 0, "upwind1": 1, "upwind2": 2, "tvd": 3}
 PREC = {"fp32": 0, "fp64": 1}
@@ -48,12 +50,17 @@ _lib = None
 
 
 def lib():
-    """Load libklb.so (raises if it is missing: no fallback)."""
+    """Load libklb.so (raises if it is missing: no fallback), or with
+    KLB_CHECKED=1 the bounds-checked libklb_checked.so."""
     global _lib
     if _lib is None:
-        if not os.path.exists(LIB_PATH):
-            raise RuntimeError(f"{LIB_PATH} is not built; run paper_1010_4124_gb300/build.py")
-        L = C.CDLL(LIB_PATH)
+        path = LIB_PATH
+        if os.environ.get("KLB_CHECKED") == "1":
+            from . import build as _build
+            path = _build.build(checked=True)
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is not built; run paper_1010_4124_gb300/build.py")
+        L = C.CDLL(path)
         vp, i64, i32 = C.c_void_p, C.c_int64, C.c_int32
         P = C.POINTER(klb_params)
         sig = {
@@ -65,6 +72,7 @@ def lib():
             "klb_get_f": (C.c_int, [vp, vp, C.c_int]),
             "klb_step": (C.c_int, [vp, i64]),
             "klb_sync": (C.c_int, [vp]),
+            "klb_debug_bounds_probe": (C.c_int, [vp]),
             "klb_moments": (C.c_int, [vp, vp, vp, vp, vp, C.c_int]),
             "klb_diagnostics": (C.c_int, [vp, vp, i64, C.POINTER(i64)]),
             "klb_step_count": (i64, [vp]),
