@@ -20,7 +20,8 @@ Prints ONE JSON line (rank 0):
                 measured copy bandwidth; traffic = ncu DRAM bytes per launch
   cpu_baseline  the FP64 oracle on the host cores, on a band of the workload
   clocks, gpu_launches, and the legs sweep (batched vs looped plain step),
-  adjoint (checkpointed reverse sweep), schemes (the convection schemes of
+  adjoint (checkpointed reverse sweep, 256^2; adjoint_4096: the FP32
+  reverse step on the 4096^2 workload), schemes (the convection schemes of
   the paper's comparison) and paper_sweeps (its Kelvin-Helmholtz studies).
 
 --impl reference times the FP64 CPU oracle (the baseline of this method: the
@@ -325,6 +326,7 @@ def run_ours(args):
         line["schemes"] = schemes_measure(args.workload, 100, torch)
     if rank == 0 and not args.no_adjoint:
         line["adjoint"] = [adjoint_measure(p, args.adjoint_steps, torch) for p in ("fp32", "fp64")]
+        line["adjoint_4096"] = adjoint_large(torch)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, samples=40, rows=1024)
     if rank == 0:
@@ -402,6 +404,34 @@ def sweep_measure(steps: int, torch):
             "speedup_vs_looped_plain": round(t_loop / t_batch, 3),
             "other_tiles": {"kernel_variant": other, "batched_gcell_s": round(cells * steps / t_other / 1e9, 4)},
             "sizes": sorted({f"{pb.nx}x{pb.ny}" for pb in pbs})}
+
+
+def adjoint_large(torch, steps: int = 20):
+    """The FP32 adjoint on the 4096 x 4096 roofline workload (sampled every
+    10 steps, a checkpoint every 10): forward plus reverse sweep of `steps`
+    steps against the plain forward, and the reverse step's share of it,
+    (adjoint - 2 forward) / steps (each reverse step also recomputes one
+    forward step from its checkpoint)."""
+    from paper_1010_4124_gb300 import inputs, klb
+    pb = inputs.roofline_4096(steps).with_(sample_every=10)
+    dev = [torch.as_tensor(a, device="cuda").contiguous() for a in inputs.fields(pb)]
+    grads = tuple(torch.empty_like(dev[0]) for _ in range(4))
+    with klb.KlbAdjoint.from_problem(pb, "fp32", checkpoint_every=10) as adj:
+        adj.forward(*dev)
+        adj.backward(1.0, 1.0, out=grads)  # warm
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        adj.forward(*dev)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        adj.backward(1.0, 1.0, out=grads)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+    t_fwd, t_all = t1 - t0, t2 - t0
+    return {"workload": f"KHI 4096x4096 FP32, {steps} steps, sampled every 10, a checkpoint every 10",
+            "adjoint_s": round(t_all, 4), "forward_with_checkpoints_s": round(t_fwd, 4),
+            "reverse_step_ms": round((t_all - 2 * t_fwd) / steps * 1e3, 3),
+            "adjoint_over_2x_forward": round(t_all / (2 * t_fwd), 3)}
 
 
 def adjoint_measure(prec: str, steps: int, torch):
