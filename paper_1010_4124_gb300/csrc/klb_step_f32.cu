@@ -91,9 +91,9 @@ cudaError_t launch_diag_f32(const StepConst<float>& c, const Geom& g, const floa
     f32_tiles(g.nx, g.ny, variant, &tiles_x, &ntiles);
     const int grid = f32_grid(g.nx, g.ny, variant);
     if (rows_of(variant) == 8)
-        diag_f32_kernel<8><<<grid, 256, 0, s>>>(c, g, ntiles, f, partials);
+        diag_f32_kernel<8><<<grid, 256, 0, s>>>(c, g, tiles_x, ntiles, f, partials);
     else
-        diag_f32_kernel<16><<<grid, 512, 0, s>>>(c, g, ntiles, f, partials);
+        diag_f32_kernel<16><<<grid, 512, 0, s>>>(c, g, tiles_x, ntiles, f, partials);
     return cudaGetLastError();
 }
 

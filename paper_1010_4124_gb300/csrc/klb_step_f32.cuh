@@ -237,26 +237,15 @@ __device__ __forceinline__ int2 tile_divmod(int t, int d, float inv_d) {
     }
     return make_int2(q, r);
 }
-// Tiles of a grid are numbered down its columns: tile l is row l mod
-// tiles_y of tile column l / tiles_y, so consecutive tiles are vertical
-// neighbours and share their halo rows.
 template <int TY>
-__device__ __forceinline__ int tiles_y_of(const Geom& g) { return (g.ny + TY - 1) / TY; }
-template <int TY>
-__device__ __forceinline__ TileInfo tile_info(int l, int tiles_y, float inv_ty) {
+__device__ __forceinline__ TileInfo tile_info(int t, int tiles_x, float inv_tx) {
     TileInfo ti;
-    const int2 qr = tile_divmod(l, tiles_y, inv_ty);
-    const int tx = qr.x;
+    const int2 qr = tile_divmod(t, tiles_x, inv_tx);
+    const int tx = qr.y;
     ti.x0 = v3::TW * tx - GX;  // interior column of lane 0
-    ti.y0 = qr.y * TY;
+    ti.y0 = qr.x * TY;
     ti.bxa = v3::TW * tx - 4;  // array column of the box start (16-byte aligned; -4 reads zeros)
     return ti;
-}
-// The contiguous run of tiles [first, last) of CTA b of G in a launch of n
-// tiles: every CTA walks down tile columns, so the next tile's halo rows are
-// the rows its previous tile has just brought into L2.
-__device__ __forceinline__ int2 cta_tiles(int b, int G, int n) {
-    return make_int2((int)(((long long)b * n) / G), (int)(((long long)(b + 1) * n) / G));
 }
 
 // Tiles of several instances (grids of one batch, or the single grid of a
@@ -306,14 +295,12 @@ __global__ void __launch_bounds__(32 * TY, 16 / TY) step_f32_kernel(const __grid
         const int inst = MULTI ? find_inst(first, ninst, t) : 0;
         if (MULTI) tile_inst[b] = inst;
         const InstDesc* D = descs + inst;
-        const int ty_n = tiles_y_of<TY>(D->g);
-        const TileInfo ti = tile_info<TY>(t - D->first_tile, ty_n, __frcp_rn((float)ty_n));
+        const TileInfo ti = tile_info<TY>(t - D->first_tile, D->tiles_x, __frcp_rn((float)D->tiles_x));
         const uint32_t bar = smem_u32(&full[b]);
         tensormap_acquire(&D->map);
         mbar_arrive_expect_tx(bar, (uint32_t)(sizeof(float) * S::BOX_FLOATS));
         tma_load_3d(smem_u32(buf + b * S::BUF_FLOATS), &D->map, ti.bxa, ti.y0, 0, bar);
     };
-    const int2 run = cta_tiles(blockIdx.x, gridDim.x, ntiles);
     __syncthreads();
     if (tid == 0) {
         mbar_init(smem_u32(&full[0]), 1);
@@ -321,7 +308,7 @@ __global__ void __launch_bounds__(32 * TY, 16 / TY) step_f32_kernel(const __grid
         mbar_init(smem_u32(&never), 1);
         fence_barrier_init();
         fence_proxy_async();
-        if (run.x < run.y) issue(run.x, 0);
+        if ((int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
     }
     __syncthreads();
 
@@ -329,18 +316,18 @@ __global__ void __launch_bounds__(32 * TY, 16 / TY) step_f32_kernel(const __grid
     const bool diag = diag_partials != nullptr;
     // fields of the instance of the current tile, read from global memory
     // only when the instance changes (tiles of one instance are contiguous)
-    int cur = -1, first_t = 0, tiles_y = 1;
-    float inv_ty = 1.f;
+    int cur = -1, first_t = 0, tiles_x = 1;
+    float inv_tx = 1.f;
     Geom g{};
     float* out = nullptr;
     int k = 0;  // local tile counter: buffer k & 1, phase (k >> 1) & 1
-    for (int t = run.x; t < run.y; ++t, ++k) {
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
         const int b = k & 1;
         // prefetch the next tile into the other buffer (last read before the
         // middle barrier of the previous tile)
-        if (tid == 0 && t + 1 < run.y) {
+        if (tid == 0 && t + (int)gridDim.x < ntiles) {
             fence_proxy_async();
-            issue(t + 1, b ^ 1);
+            issue(t + gridDim.x, b ^ 1);
         }
         // A wait that gives up is reported at the barrier in the middle of
         // the tile; until then the thread computes on whatever the buffer
@@ -354,12 +341,12 @@ __global__ void __launch_bounds__(32 * TY, 16 / TY) step_f32_kernel(const __grid
             g = D->g;
             out = D->out;
             first_t = D->first_tile;
-            tiles_y = tiles_y_of<TY>(g);
-            inv_ty = __frcp_rn((float)tiles_y);
+            tiles_x = D->tiles_x;
+            inv_tx = __frcp_rn((float)tiles_x);
             cur = inst;
         }
         const float* tile = buf + b * S::BUF_FLOATS;
-        const TileInfo ti = tile_info<TY>(t - first_t, tiles_y, inv_ty);
+        const TileInfo ti = tile_info<TY>(t - first_t, tiles_x, inv_tx);
         const int ix = ti.x0 + lane, iy = ti.y0 + ty;
         const int s = lane + 4;  // smem column of the node
         const int r = ty + 3;    // smem row of the node
@@ -398,7 +385,8 @@ __global__ void __launch_bounds__(32 * TY, 16 / TY) step_f32_kernel(const __grid
                 atomicOr(err, ERR_TIMEOUT);
                 // let both copies that may be in flight land before leaving
                 mbar_wait_bounded(smem_u32(&full[b]), (k >> 1) & 1, kDrainPolls);
-                if (t + 1 < run.y) mbar_wait_bounded(smem_u32(&full[b ^ 1]), ((k + 1) >> 1) & 1, kDrainPolls);
+                if (t + (int)gridDim.x < ntiles)
+                    mbar_wait_bounded(smem_u32(&full[b ^ 1]), ((k + 1) >> 1) & 1, kDrainPolls);
             }
             __syncthreads();
             return;
@@ -428,21 +416,19 @@ __global__ void __launch_bounds__(32 * TY, 16 / TY) step_f32_kernel(const __grid
     if (diag) diag_block_reduce<S::NT>(acc, diag_partials + 8ll * blockIdx.x);
 }
 
-// Diagnostics of a state with the same tiles, per-CTA tile runs and block
+// Diagnostics of a state with the same tiles, per-CTA tile order and block
 // reduction as the fused path inside the step kernel, so that both give the
-// same bits: CTA `cta` of `ncta` takes its run of tiles (cta_tiles) and
-// writes one partial record.
+// same bits: CTA `cta` of `ncta` takes tiles cta, cta + ncta, ... and writes
+// one partial record.
 template <int TY>
-__device__ __forceinline__ void diag_cta(const StepConst<float>& c, const Geom& g, int ntiles,
+__device__ __forceinline__ void diag_cta(const StepConst<float>& c, const Geom& g, int tiles_x, int ntiles,
                                          const float* __restrict__ f, double* __restrict__ partial, int cta,
                                          int ncta) {
     const int tid = threadIdx.x, ty = tid >> 5, lane = tid & 31;
-    const int tiles_y = tiles_y_of<TY>(g);
-    const float inv_ty = __frcp_rn((float)tiles_y);
-    const int2 run = cta_tiles(cta, ncta, ntiles);
+    const float inv_tx = __frcp_rn((float)tiles_x);
     // the node of tile t for this thread, its activity and its 19 values
     auto load = [&](int t, float fl[NQ]) {
-        const TileInfo ti = tile_info<TY>(t, tiles_y, inv_ty);
+        const TileInfo ti = tile_info<TY>(t, tiles_x, inv_tx);
         const int ix = ti.x0 + lane, iy = ti.y0 + ty;
         const bool active = ix >= 0 && ix < g.nx && iy < g.ny;
 #pragma unroll
@@ -454,9 +440,9 @@ __device__ __forceinline__ void diag_cta(const StepConst<float>& c, const Geom& 
     // the loads of the next tile are issued before the current one is reduced
     // (two tiles in flight per thread); the accumulation order is unchanged
     float cur[NQ], nxt[NQ];
-    bool act = run.x < run.y ? load(run.x, cur) : false;
-    for (int t = run.x; t < run.y; ++t) {
-        const bool act_n = t + 1 < run.y ? load(t + 1, nxt) : false;
+    bool act = cta < ntiles ? load(cta, cur) : false;
+    for (int t = cta; t < ntiles; t += ncta) {
+        const bool act_n = t + ncta < ntiles ? load(t + ncta, nxt) : false;
         acc.add(ArithF32::node_state(c, cur), act);
 #pragma unroll
         for (int q = 0; q < NQ; ++q) cur[q] = nxt[q];
@@ -466,10 +452,10 @@ __device__ __forceinline__ void diag_cta(const StepConst<float>& c, const Geom& 
 }
 
 template <int TY>
-__global__ void __launch_bounds__(32 * TY) diag_f32_kernel(const StepConst<float> c, const Geom g, int ntiles,
-                                                           const float* __restrict__ f,
+__global__ void __launch_bounds__(32 * TY) diag_f32_kernel(const StepConst<float> c, const Geom g, int tiles_x,
+                                                           int ntiles, const float* __restrict__ f,
                                                            double* __restrict__ partials) {
-    diag_cta<TY>(c, g, ntiles, f, partials + 8ll * blockIdx.x, blockIdx.x, gridDim.x);
+    diag_cta<TY>(c, g, tiles_x, ntiles, f, partials + 8ll * blockIdx.x, blockIdx.x, gridDim.x);
 }
 
 // The stand-alone reductions of several members in one launch: CTA b belongs
@@ -487,7 +473,7 @@ __global__ void __launch_bounds__(32 * TY) diag_f32_batch_kernel(const StepConst
     if (!KLB_DUE_BIT(due, lo)) return;  // uniform across the CTA
     const DiagJob& J = jobs[lo];
     const int v = (int)blockIdx.x - J.first_cta;
-    diag_cta<TY>(c, J.g, J.ntiles, J.f, J.partials + 8ll * v, v, J.grid);
+    diag_cta<TY>(c, J.g, J.tiles_x, J.ntiles, J.f, J.partials + 8ll * v, v, J.grid);
 }
 
 // dynamic shared memory of the kernel instance, set once per process

@@ -1,5 +1,5 @@
-"""The FP32 kernels split a tile index t into (tile column, tile row) =
-divmod(t, d), d the tiles per column, without an integer division: q = trunc(rn(t * rn(1 / d))) in single
+"""The FP32 kernels split a tile index t into (row, column) = divmod(t, d)
+without an integer division: q = trunc(rn(t * rn(1 / d))) in single
 precision, then one correction step.  The same arithmetic in numpy float32
 (IEEE single, round to nearest like the device's __frcp_rn and __fmul_rn)
 must give divmod exactly for every 0 <= t < 2^24 and d >= 1, the range the
