@@ -326,7 +326,8 @@ def run_ours(args):
         line["schemes"] = schemes_measure(args.workload, 100, torch)
     if rank == 0 and not args.no_adjoint:
         line["adjoint"] = [adjoint_measure(p, args.adjoint_steps, torch) for p in ("fp32", "fp64")]
-        line["adjoint_4096"] = adjoint_large(torch)
+        if not args.no_adjoint_4096:
+            line["adjoint_4096"] = adjoint_large(torch)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, samples=40, rows=1024)
     if rank == 0:
@@ -665,6 +666,7 @@ def main():
     ap.add_argument("--no-schemes", action="store_true")
     ap.add_argument("--no-physics", action="store_true")
     ap.add_argument("--adjoint-steps", type=int, default=2000)
+    ap.add_argument("--no-adjoint-4096", action="store_true", help="skip the FP32 adjoint on the 4096^2 workload")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
