@@ -52,7 +52,12 @@ extern "C" {
 #define KLB_E_BOUNDS (-8)         /* bounds-checked build (libklb_checked.so) only: a kernel formed
                                    * an index outside its buffer; the access was skipped */
 
-typedef enum { KLB_BC_PERIODIC = 0, KLB_BC_OUTFLOW = 1, KLB_BC_FIXED_EQ = 2 } klb_bc;
+/* Boundary kinds of Sec. III.B and IV: periodic wrap, outflow (zeroth-order
+ * extrapolation, Eqs. 63-64), fixed equilibrium ghosts (Eq. 57).  KLB_BC_HALO
+ * (y sides only) marks a side whose three ghost rows another grid supplies:
+ * the step neither writes nor reads anything else there; the slab engine
+ * (klb_slabs_*) fills them from the neighbouring slab before every step. */
+typedef enum { KLB_BC_PERIODIC = 0, KLB_BC_OUTFLOW = 1, KLB_BC_FIXED_EQ = 2, KLB_BC_HALO = 3 } klb_bc;
 typedef enum { KLB_FP32 = 0, KLB_FP64 = 1 } klb_prec;
 
 /* Convection scheme of the face fluxes h (Eq. 47).  The paper's method is
@@ -209,6 +214,50 @@ int klb_get_variant(const klb_t* h);
  * guards and refuses the call (KLB_E_INVAL) without launching anything.
  * This is a debugging aid with no counterpart in the paper. */
 int klb_debug_bounds_probe(klb_t* h);
+
+/* ---------------------------------------------------------------------------
+ * Slab decomposition (the domain decomposition of Eq. 47 over the grid of
+ * Sec. III.B that a step spread over several devices would use; here all
+ * slabs live on the current device).  The grid of `p` is cut in y into n
+ * slabs of contiguous rows; each slab is a grid of its own (klb_t with its
+ * own buffers) whose sides between slabs are KLB_BC_HALO.  Every step first
+ * copies, in one kernel, the three rows next to each cut (19 planes, interior
+ * columns) into the neighbouring slab's ghost rows (with a periodic y, across
+ * the domain's ends too), then steps every slab: the result is bitwise that
+ * of the whole grid.  Slabs hold at least 3 rows (the depth of the ghost
+ * layer).  Errors as for klb_create / klb_step; the message of a failed call
+ * is in klb_slabs_last_error.
+ * ------------------------------------------------------------------------- */
+typedef struct klb_slabs klb_slabs_t;
+
+/* Host only (no device work): the rows of slab k of n over ny rows, as
+ * balanced as possible (the first ny % n slabs one row more): row0[k] and
+ * rows[k], arrays of n entries owned by the caller.  KLB_E_INVAL when n < 1
+ * or a slab would hold fewer than 3 rows. */
+int klb_slab_partition(int32_t ny, int32_t n, int32_t* row0, int32_t* rows);
+
+/* Host only: the slabs whose rows fill the ghost rows of slab k -- *below
+ * supplies rows -3..-1, *above rows rows[k]..rows[k]+2 -- or -1 where the
+ * side is the domain's own (outflow, fixed-equilibrium) side.  With a
+ * periodic y the neighbours wrap (n = 1: the slab is its own neighbour and
+ * keeps the periodic sides). */
+int klb_slab_neighbors(const klb_params* p, int32_t n, int32_t k, int32_t* below, int32_t* above);
+
+/* n slabs of the grid of p (p->bc_y_* are the domain's y sides). */
+int klb_slabs_create(const klb_params* p, int32_t n, klb_slabs_t** out);
+void klb_slabs_destroy(klb_slabs_t* s);
+/* The whole grid's initial fields [ny][nx] (host or device): each slab takes
+ * its rows. */
+int klb_slabs_init_fields(klb_slabs_t* s, const double* rho, const double* ux, const double* uy, const double* T,
+                          int on_device);
+/* n steps of every slab (asynchronous, on the slabs' shared stream). */
+int klb_slabs_step(klb_slabs_t* s, int64_t n);
+/* The whole grid's distribution [19][ny][nx] assembled from the slabs
+ * (synchronises). */
+int klb_slabs_get_f(klb_slabs_t* s, double* f, int on_device);
+/* Slab k's handle (owned by the slab set) or NULL. */
+klb_t* klb_slabs_member(klb_slabs_t* s, int32_t k);
+const char* klb_slabs_last_error(const klb_slabs_t* s);
 
 /* ---------------------------------------------------------------------------
  * Batched engine (the D_v x D_rho sweeps of Sec. IV).  A batch holds n FP32

@@ -292,7 +292,7 @@ int klb_adjoint_create(const klb_params* p, int64_t nsteps, int32_t checkpoint_e
         return afail(nullptr, KLB_E_INVAL, "sample_every must be >= 1 and divide nsteps");
     const int bcs[4] = {p->bc_x_lo, p->bc_x_hi, p->bc_y_lo, p->bc_y_hi};
     for (int b : bcs)
-        if (b == KLB_BC_FIXED_EQ)
+        if (b == KLB_BC_FIXED_EQ || b == KLB_BC_HALO)
             return afail(nullptr, KLB_E_INVAL, "the adjoint supports periodic and outflow sides only");
     if (p->scheme != KLB_WENO5) return afail(nullptr, KLB_E_INVAL, "the adjoint differentiates the WENO5 step only");
     klb_params q = *p;

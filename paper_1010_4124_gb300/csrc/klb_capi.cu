@@ -25,7 +25,7 @@ int fdlb::handle_fail(klb_t* h, int code, const std::string& msg) { return fail(
 int fdlb::bounds_flags() {
 #ifdef KLB_CHECK_BOUNDS
     return bounds_flag_aux_f32() | bounds_flag_aux_f64() | bounds_flag_step_f32() | bounds_flag_step_f32_lo() |
-           bounds_flag_step_f64() | bounds_flag_adjoint();
+           bounds_flag_step_f64() | bounds_flag_adjoint() | bounds_flag_slabs();
 #else
     return 0;
 #endif
@@ -211,7 +211,9 @@ int klb_create(const klb_params* pin, klb_t** out) {
         return fail(nullptr, KLB_E_INVAL, "ring speeds must be distinct");
     const int bcs[4] = {p.bc_x_lo, p.bc_x_hi, p.bc_y_lo, p.bc_y_hi};
     for (int b : bcs)
-        if (b < 0 || b > 2) return fail(nullptr, KLB_E_INVAL, "unknown boundary kind");
+        if (b < 0 || b > 3) return fail(nullptr, KLB_E_INVAL, "unknown boundary kind");
+    if (p.bc_x_lo == KLB_BC_HALO || p.bc_x_hi == KLB_BC_HALO)
+        return fail(nullptr, KLB_E_INVAL, "halo sides are y sides (slabs cut the grid in y)");
     if ((p.bc_x_lo == KLB_BC_PERIODIC) != (p.bc_x_hi == KLB_BC_PERIODIC) ||
         (p.bc_y_lo == KLB_BC_PERIODIC) != (p.bc_y_hi == KLB_BC_PERIODIC))
         return fail(nullptr, KLB_E_INVAL, "a periodic side must pair with a periodic side");

@@ -101,7 +101,7 @@ struct Geom {
     int nx, ny;          // interior size
     int px;              // row pitch (elements)
     long long plane;     // plane stride (elements)
-    int bcx_lo, bcx_hi, bcy_lo, bcy_hi;  // 0 periodic, 1 outflow, 2 fixed
+    int bcx_lo, bcx_hi, bcy_lo, bcy_hi;  // 0 periodic, 1 outflow, 2 fixed, 3 halo (rows of another grid; no images)
 };
 
 // Macroscopic state of one node and the equilibrium factors derived from it.

@@ -122,6 +122,7 @@ int bounds_flag_step_f32();
 int bounds_flag_step_f32_lo();
 int bounds_flag_step_f64();
 int bounds_flag_adjoint();
+int bounds_flag_slabs();
 int bounds_flags();
 // bounds-checked builds only: one guarded store past the end of a buffer of
 // n floats (skipped and flagged); cudaErrorNotSupported elsewhere

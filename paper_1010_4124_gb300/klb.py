@@ -22,7 +22,7 @@ LIB_CHECKED_PATH = os.path.join(HERE, "libklb_checked.so")
 KLB_OK = 0
 ERRORS = {-1: "KLB_E_INVAL", -2: "KLB_E_NOMEM", -3: "KLB_E_CUDA", -4: "KLB_E_NONFINITE",
           -5: "KLB_E_DEVICE_TIMEOUT", -6: "KLB_E_STATE", -7: "KLB_E_IO", -8: "KLB_E_BOUNDS"}
-BC = {"periodic": 0, "outflow": 1, "fixed_eq": 2}
+BC = {"periodic": 0, "outflow": 1, "fixed_eq": 2, "halo": 3}
 SCHEMES = {"weno5": 0, "upwind1": 1, "upwind2": 2, "tvd": 3}
 PREC = {"fp32": 0, "fp64": 1}
 
@@ -85,6 +85,15 @@ def lib():
             "klb_debug_inject_wait_timeout": (C.c_int, [vp, i64]),
             "klb_set_variant": (C.c_int, [vp, C.c_int]),
             "klb_get_variant": (C.c_int, [vp]),
+            "klb_slab_partition": (C.c_int, [i32, i32, C.POINTER(i32), C.POINTER(i32)]),
+            "klb_slab_neighbors": (C.c_int, [P, i32, i32, C.POINTER(i32), C.POINTER(i32)]),
+            "klb_slabs_create": (C.c_int, [P, i32, C.POINTER(vp)]),
+            "klb_slabs_destroy": (None, [vp]),
+            "klb_slabs_init_fields": (C.c_int, [vp, vp, vp, vp, vp, C.c_int]),
+            "klb_slabs_step": (C.c_int, [vp, i64]),
+            "klb_slabs_get_f": (C.c_int, [vp, vp, C.c_int]),
+            "klb_slabs_member": (vp, [vp, i32]),
+            "klb_slabs_last_error": (C.c_char_p, [vp]),
             "klb_batch_create": (C.c_int, [C.POINTER(klb_params), C.c_int, C.POINTER(vp)]),
             "klb_batch_destroy": (None, [vp]),
             "klb_batch_size": (C.c_int, [vp]),
@@ -288,6 +297,90 @@ def _bcheck(b, code):
     if code != KLB_OK:
         msg = lib().klb_batch_last_error(b)
         raise KlbError(code, msg.decode() if msg else "")
+
+
+def slab_partition(ny: int, n: int):
+    """(row0, rows) of the n slabs of ny rows (klb_slab_partition; host only)."""
+    r0, r = (C.c_int32 * n)(), (C.c_int32 * n)()
+    code = lib().klb_slab_partition(int(ny), int(n), r0, r)
+    if code != KLB_OK:
+        raise KlbError(code, f"{ny} rows cannot be cut into {n} slabs of at least 3 rows")
+    return list(r0), list(r)
+
+
+def slab_neighbors(params: klb_params, n: int, k: int):
+    """(below, above): the slabs that fill slab k's ghost rows, -1 for the
+    domain's own sides (klb_slab_neighbors; host only)."""
+    b, a = C.c_int32(), C.c_int32()
+    code = lib().klb_slab_neighbors(C.byref(params), int(n), int(k), C.byref(b), C.byref(a))
+    if code != KLB_OK:
+        raise KlbError(code, "invalid slab index")
+    return b.value, a.value
+
+
+class KlbSlabs:
+    """The grid cut in y into n slabs, each a grid of its own, the ghost rows
+    at every cut copied from the neighbour before each step (klb_slabs_*)."""
+
+    def __init__(self, params: klb_params, n: int):
+        s = C.c_void_p()
+        code = lib().klb_slabs_create(C.byref(params), int(n), C.byref(s))
+        if code != KLB_OK:
+            raise KlbError(code, (lib().klb_slabs_last_error(None) or b"").decode())
+        self.s, self.n = s, n
+        self.nx, self.ny = params.nx, params.ny
+        self.row0, self.rows = slab_partition(params.ny, n)
+        self.members = []
+        for k in range(n):
+            q = klb_params()
+            C.pointer(q)[0] = params
+            q.ny = self.rows[k]
+            self.members.append(Klb(q, _borrowed=lib().klb_slabs_member(s, k)))
+
+    @classmethod
+    def from_problem(cls, pb, n: int, precision="fp32", stream=None, **kw):
+        return cls(make_params(pb.nx, pb.ny, pb.dx, pb.dy, pb.dt, pb.tau, v=pb.v, bc_x=pb.bc_x, bc_y=pb.bc_y,
+                               precision=precision, sample_every=kw.pop("sample_every", 0), stream=stream, **kw), n)
+
+    def _check(self, code):
+        if code != KLB_OK:
+            raise KlbError(code, (lib().klb_slabs_last_error(self.s) or b"").decode())
+
+    def init_fields(self, rho, ux, uy, T):
+        ptrs = [_ptr(x, self.nx * self.ny) for x in (rho, ux, uy, T)]
+        ond = {p[1] for p in ptrs}
+        if len(ond) != 1:
+            raise TypeError("all four fields must live on the same side (host or device)")
+        self._check(lib().klb_slabs_init_fields(self.s, *[p[0] for p in ptrs], ond.pop()))
+
+    def step(self, n: int):
+        self._check(lib().klb_slabs_step(self.s, int(n)))
+
+    def get_f(self, out=None):
+        if out is None:
+            out = np.empty((19, self.ny, self.nx))
+        p, on_device = _ptr(out, 19 * self.nx * self.ny)
+        self._check(lib().klb_slabs_get_f(self.s, p, on_device))
+        return out
+
+    def close(self):
+        if getattr(self, "s", None):
+            for m in self.members:
+                m.h = None
+            lib().klb_slabs_destroy(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 class KlbBatch:
