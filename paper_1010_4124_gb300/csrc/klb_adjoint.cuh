@@ -17,8 +17,6 @@
 //   * sources and the initial state: dK/df for K = sum rho u_y^2 / 2, and
 //     (d f^(0) / d(rho, u_x, u_y, T))^T lambda^0 for the initial fields.
 #pragma once
-#include <type_traits>
-
 #include "klb_device.cuh"
 #include "klb_launch.h"
 
@@ -80,48 +78,6 @@ __device__ __forceinline__ T weno5_grad(T a, T b, T c, T d, T e, T eps34, T g[5]
     g[3] = g3 + g4;
     g[4] = -g4;
     return c + hh;
-}
-
-// The same gradient for two independent faces at once in FP32 (packed f32x2
-// arithmetic, one instruction for both lanes; the reciprocals per lane).
-__device__ __forceinline__ void weno5_grad2(float2 a, float2 b, float2 c, float2 d, float2 e, float eps34,
-                                            float2 g[5]) {
-    auto P = [](float k) { return make_float2(k, k); };
-    const float2 m1 = P(-1.f);
-    const float2 D1 = __ffma2_rn(b, m1, a), D2 = __ffma2_rn(b, m1, c);
-    const float2 D3 = __ffma2_rn(c, m1, d), E4 = __ffma2_rn(e, m1, d);
-    const float2 ep = P(eps34);
-    const float2 s1 = __ffma2_rn(D1, __ffma2_rn(P(2.75f), D2, D1), __ffma2_rn(P(2.5f), __fmul2_rn(D2, D2), ep));
-    const float2 s2 = __ffma2_rn(D2, __ffma2_rn(P(-1.25f), D3, D2), __ffma2_rn(D3, D3, ep));
-    const float2 s3 = __ffma2_rn(E4, __ffma2_rn(P(2.75f), D3, E4), __ffma2_rn(P(2.5f), __fmul2_rn(D3, D3), ep));
-    const float2 r1 = make_float2(rcp_approx(s1.x), rcp_approx(s1.y));
-    const float2 r2 = make_float2(rcp_approx(s2.x), rcp_approx(s2.y));
-    const float2 r3 = make_float2(rcp_approx(s3.x), rcp_approx(s3.y));
-    const float2 w1 = __fmul2_rn(r1, r1), w2 = __fmul2_rn(r2, r2), w3 = __fmul2_rn(r3, r3);
-    const float2 t3 = __fadd2_rn(D3, D3);
-    const float2 G1 = __ffma2_rn(P(5.f / 6.f), D2, __fmul2_rn(P(1.f / 3.f), D1));
-    const float2 G2 = __fadd2_rn(D2, t3), G3 = __ffma2_rn(P(0.5f), E4, t3);
-    const float2 den = __ffma2_rn(P(6.f), w2, __ffma2_rn(P(3.f), w3, w1));
-    const float2 rD = make_float2(rcp_approx(den.x), rcp_approx(den.y));
-    const float2 hh = __fmul2_rn(__ffma2_rn(G1, w1, __ffma2_rn(G2, w2, __fmul2_rn(G3, w3))), rD);
-    const float2 o1 = __fmul2_rn(w1, rD), o2 = __fmul2_rn(w2, rD), o3 = __fmul2_rn(w3, rD);
-    const float2 m = __fmul2_rn(P(-2.f), rD);
-    const float2 b1 = __fmul2_rn(__fmul2_rn(__fadd2_rn(G1, __fmul2_rn(m1, hh)), __fmul2_rn(w1, r1)), m);
-    const float2 b2 = __fmul2_rn(__fmul2_rn(__ffma2_rn(P(-6.f), hh, G2), __fmul2_rn(w2, r2)), m);
-    const float2 b3 = __fmul2_rn(__fmul2_rn(__ffma2_rn(P(-3.f), hh, G3), __fmul2_rn(w3, r3)), m);
-    const float2 g1 = __ffma2_rn(b1, __ffma2_rn(P(2.f), D1, __fmul2_rn(P(2.75f), D2)), __fmul2_rn(P(1.f / 3.f), o1));
-    const float2 g2 = __ffma2_rn(b2, __ffma2_rn(P(2.f), D2, __fmul2_rn(P(-1.25f), D3)),
-                                 __ffma2_rn(b1, __ffma2_rn(P(2.75f), D1, __fmul2_rn(P(5.f), D2)),
-                                            __ffma2_rn(P(5.f / 6.f), o1, o2)));
-    const float2 g3 = __ffma2_rn(b3, __ffma2_rn(P(2.75f), E4, __fmul2_rn(P(5.f), D3)),
-                                 __ffma2_rn(b2, __ffma2_rn(P(2.f), D3, __fmul2_rn(P(-1.25f), D2)),
-                                            __fmul2_rn(P(2.f), __fadd2_rn(o2, o3))));
-    const float2 g4 = __ffma2_rn(b3, __ffma2_rn(P(2.f), E4, __fmul2_rn(P(2.75f), D3)), __fmul2_rn(P(0.5f), o3));
-    g[0] = g1;
-    g[1] = __ffma2_rn(g1, m1, __fmul2_rn(g2, m1));
-    g[2] = __fadd2_rn(__ffma2_rn(g3, m1, g2), P(1.f));
-    g[3] = __fadd2_rn(g3, g4);
-    g[4] = __fmul2_rn(g4, m1);
 }
 
 // Moments of one node (Eq. 10) in the form the derivatives use.
@@ -455,31 +411,8 @@ __device__ __forceinline__ void adj_tile_body(const StepConst<T>& c, const Geom&
         for (int e = 0; e < 5; ++e) gy[e][s][cl] = mu * gr[e];
     };
     if (SX != 0) {
-        if constexpr (std::is_same<T, float>::value && SY != 0) {
-            // the thread's x face (w, l) and y face (w, l) as one packed pair
-            const float* row = fs[w + 5];
-            const int x = l + 8;
-            float2 st[5];
-#pragma unroll
-            for (int k = 0; k < 5; ++k) {
-                const float fx = SX > 0 ? row[l + 3 + k] : row[l + 8 - k];
-                const float fy = SY > 0 ? fs[w + k][x] : fs[w + 5 - k][x];
-                st[k] = __fmul2_rn(make_float2(vx, vy), make_float2(fx, fy));
-            }
-            float2 gr[5];
-            weno5_grad2(st[0], st[1], st[2], st[3], st[4], e34, gr);
-            const float2 mu = make_float2(c.cx[q] * (ls[w + 3][l + 6] - ls[w + 3][l + 5]),
-                                          c.cy[q] * (ls[w + 1][x] - ls[w][x]));
-#pragma unroll
-            for (int e = 0; e < 5; ++e) {
-                const float2 v = __fmul2_rn(mu, gr[e]);
-                gx[e][w][l] = v.x;
-                gy[e][w][l] = v.y;
-            }
-        } else {
-            face_x(w, l);
-            if (SY != 0) face_y(w, l);
-        }
+        face_x(w, l);
+        if (SY != 0) face_y(w, l);
         if (w < 5) {
             if (SY != 0) face_y(TY + w, l);
         } else if (l < 20) {
