@@ -350,18 +350,19 @@ __global__ void __launch_bounds__(kNodeSeg) adj_node_kernel(const __grid_constan
     KLB_GUARD(4 * n + t, 5 * n) N[4 * n + t] = m.uy;
 }
 
-// Tiles of the reverse step: 32 x TY positions of the extended grid (columns
-// -4 .. nx + 2, rows -3 .. ny + 2: interior nodes and the ghost positions
-// whose sums the fold kernel adds back).  One CTA per (tile, velocity q).
-// Both staged boxes are BW = 48 positions wide and start 8 positions left of
-// the tile's lane 0 (array column 32 tx - 8: 16-byte aligned for TMA): the f
-// box holds rows -5 .. TY + 4 of the tile, the lambda box rows -3 .. TY + 2.
+// Tiles of the reverse step: 32 x TY interior positions (tile (bx, by) starts
+// at node (32 bx, TY by)).  One CTA per (tile, velocity q).  Both staged boxes
+// are BW = 48 positions wide and start 8 positions left of the tile's lane 0
+// (array column 32 bx - 4: 16-byte aligned for TMA): the f box holds rows
+// -5 .. TY + 4 of the tile, the lambda box rows -3 .. TY + 2.  The ghost
+// positions next to the grid's edges (whose sums the fold kernel adds back)
+// are gathered by the tiles at those edges, from faces they hold anyway.
 template <typename T, int TY>
 struct AdjTile {
     static constexpr int TX = 32, BW = 48;
     static constexpr int FR = TY + 10, LR = TY + 6;
-    static __host__ __device__ int tiles_x(int nx) { return (nx + GX + 3 + TX - 1) / TX; }
-    static __host__ __device__ int tiles_y(int ny) { return (ny + 2 * GY + TY - 1) / TY; }
+    static __host__ __device__ int tiles_x(int nx) { return (nx + TX - 1) / TX; }
+    static __host__ __device__ int tiles_y(int ny) { return (ny + TY - 1) / TY; }
     static_assert((BW * sizeof(T)) % 16 == 0, "TMA box rows of 16-byte multiples");
     static_assert((FR * BW * sizeof(T)) % 128 == 0 && (LR * BW * sizeof(T)) % 128 == 0, "boxes keep 128-byte alignment");
 };
@@ -421,6 +422,51 @@ __device__ __forceinline__ void adj_tile_body(const StepConst<T>& c, const Geom&
         }
     }
     __syncthreads();
+    // ghost positions beyond the tile's own columns or rows at the grid's
+    // edges: the 3 columns left of column 0 (and right of the last tile, past
+    // its lanes) in the tile's rows, the 3 rows below row 0 (and above the last
+    // tile row) in its columns; each sums the face entries whose slot falls
+    // inside the tile's face arrays (the others belong to faces off the grid)
+    {
+        // the last tile column (row) takes the ghost columns (rows) past its lanes
+        const int xr_lo = x0 == 0 ? 3 : 0;
+        const int xr_hi = x0 + TX >= g.nx ? max(0, g.nx + 3 - (x0 + TX)) : 0;
+        const int yr_lo = y0 == 0 ? 3 : 0;
+        const int yr_hi = y0 + TY >= g.ny ? max(0, g.ny + 3 - (y0 + TY)) : 0;
+        int k = threadIdx.x;
+        const int nxr = (xr_lo + xr_hi) * TY;
+        if (k < nxr) {  // an x rim position: column p, row y0 + r
+            const int r = k / (xr_lo + xr_hi), m = k - r * (xr_lo + xr_hi);
+            const int p = m < xr_lo ? m - 3 : x0 + TX + (m - xr_lo);
+            const int y = y0 + r;
+            if (SX != 0 && y < g.ny) {
+                T acc = T(0);
+#pragma unroll
+                for (int e = 0; e < 5; ++e) {
+                    const int sl = SX > 0 ? p - x0 + 5 - e : p - x0 + e;
+                    if (sl >= 0 && sl < TX + 5) acc += gx[e][r][sl];
+                }
+                const long long at = q * g.plane + (long long)(y + GY) * g.px + (p + GX);
+                KLB_GUARD(at, NQ * g.plane) lam_out[at] = acc;
+            }
+        } else if ((k -= nxr) < (yr_lo + yr_hi) * TX) {  // a y rim position: row p, column x0 + l
+            const int r = k / TX, cl = k - r * TX;
+            const int p = r < yr_lo ? r - 3 : y0 + TY + (r - yr_lo);
+            const int x = x0 + cl;
+            if (x < g.nx) {
+                T acc = T(0);
+                if (SY != 0) {
+#pragma unroll
+                    for (int e = 0; e < 5; ++e) {
+                        const int sl = SY > 0 ? p - y0 + 5 - e : p - y0 + e;
+                        if (sl >= 0 && sl < TY + 5) acc += gy[e][sl][cl];
+                    }
+                }
+                const long long at = q * g.plane + (long long)(p + GY) * g.px + (x + GX);
+                KLB_GUARD(at, NQ * g.plane) lam_out[at] = acc;
+            }
+        }
+    }
     const int x = x0 + l, y = y0 + w;
     const bool xin = x >= 0 && x < g.nx, yin = y >= 0 && y < g.ny;
     const bool xg = (x >= -GX + 1 && x < 0) || (x >= g.nx && x < g.nx + 3);
@@ -474,15 +520,16 @@ __global__ void __launch_bounds__(32 * TY) adj_tile_kernel(const __grid_constant
     const int q = blockIdx.y;
     const int tiles_x = A::tiles_x(g.nx);
     const int by = (int)blockIdx.x / tiles_x, bx = (int)blockIdx.x - by * tiles_x;
-    const int x0 = bx * TX - GX, y0 = by * TY - GY;
+    const int x0 = bx * TX, y0 = by * TY;
     const uint32_t b = smem_u32(&bar);
     if (threadIdx.x == 0) {
         mbar_init(b, 1);
         fence_barrier_init();
         fence_proxy_async();
         mbar_arrive_expect_tx(b, (uint32_t)(sizeof(T) * A::BW * (A::FR + A::LR)));
-        tma_load_3d(smem_u32(&fs[0][0]), &fmap, bx * TX - 8, by * TY - 5, q, b);
-        tma_load_3d(smem_u32(&ls[0][0]), &lmap, bx * TX - 8, by * TY - 3, q, b);
+        // box origins (array coordinates): column x0 - 8 + GX, rows y0 - 5 + GY and y0 - 3 + GY
+        tma_load_3d(smem_u32(&fs[0][0]), &fmap, x0 - 8 + GX, y0 - 5 + GY, q, b);
+        tma_load_3d(smem_u32(&ls[0][0]), &lmap, x0 - 8 + GX, y0 - 3 + GY, q, b);
     }
     __syncthreads();
     const bool late = !mbar_wait_bounded(b, 0, spin_limit);

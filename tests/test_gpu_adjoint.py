@@ -38,12 +38,14 @@ def _oracle_objective(pb, fields, cs=False):
     return ke, gamma
 
 
-@pytest.mark.parametrize("ckpt,size", [(7, None), (1, None), (100, None), (7, (70, 45)), (4, (45, 70)), (3, (5, 12))])
+@pytest.mark.parametrize("ckpt,size", [(7, None), (1, None), (100, None), (7, (70, 45)), (4, (45, 70)), (3, (5, 12)),
+                                       (5, (64, 32))])
 def test_dot_product_with_oracle_tangent(ckpt, size):
     # size None: the small grid (one tile column); (70, 45) and (45, 70):
     # several tiles of the fused reverse step in x and y, ragged at the edges;
-    # (5, 12): narrower than the 6 nodes the in-kernel fold of ghost images
-    # assumes (the periodic wrap images a node more than once)
+    # (5, 12): narrower than the periodic wrap's depth (a node imaged more than
+    # once); (64, 32): whole tiles, so the ghost positions at every edge lie
+    # past the tiles' own columns and rows
     pb = _small() if size is None else inputs.khi(size[0], size[1], 30, Dv=2.0, Drho=3.0, sample_every=5)
     fields = inputs.fields(pb)
     p = oracle_params(pb)
