@@ -114,7 +114,11 @@ void klb_destroy(klb_t* h);
  * at every node, ghost nodes filled, and the fixed-equilibrium ghost values of
  * Eq. 57 taken from the edge nodes of these fields.  Fields are [ny][nx]
  * doubles; T > 0 and rho > 0.  Resets the step counter and the diagnostics
- * series (the state at step 0 is sampled when sample_every > 0).  Errors:
+ * series (the state at step 0 is sampled when sample_every > 0).  Enqueued
+ * on the handle's stream: host fields in pinned (page-locked, mapped) memory
+ * are read by the kernel directly across the host link, other host fields
+ * are first copied to device staging; either way the host arrays must stay
+ * unchanged until the stream has passed the call (klb_sync).  Errors:
  * KLB_E_INVAL (NULL pointer), KLB_E_CUDA. */
 int klb_init_fields(klb_t* h, const double* rho, const double* ux, const double* uy,
                     const double* T, int on_device);
@@ -135,12 +139,14 @@ int klb_get_f(klb_t* h, double* f, int on_device);
 int klb_step(klb_t* h, int64_t n);
 
 /* Wait for the handle's stream; report device-side errors recorded since the
- * last synchronising call (KLB_E_DEVICE_TIMEOUT, KLB_E_NONFINITE). */
+ * last synchronising call (KLB_E_DEVICE_TIMEOUT, KLB_E_NONFINITE; KLB_E_BOUNDS
+ * in the bounds-checked build). */
 int klb_sync(klb_t* h);
 
 /* Macroscopic fields (Eq. 10) of the current state into caller-owned [ny][nx]
  * double arrays: rho, u_x, u_y and T (P = rho T).  Any pointer may be NULL to
- * skip that field.  Synchronises. */
+ * skip that field.  Host arrays in pinned memory are written by the kernel
+ * directly, others through device staging.  Synchronises. */
 int klb_moments(klb_t* h, double* rho, double* ux, double* uy, double* T, int on_device);
 
 /* Averaged density profile of the mixing layer (Sec. IV.A, Fig. 4): the

@@ -8,8 +8,9 @@
 
 namespace fdlb {
 
-// f := f^(0)(rho, u, T) at every interior node (Eq. 28), written to both
-// ping-pong buffers with ghost images.
+// f := f^(0)(rho, u, T) at every interior node (Eq. 28), with ghost images,
+// written to buffer a (and to b when it is not NULL).  The fields may live in
+// host memory the device can read (pinned, mapped).
 template <typename T>
 __global__ void init_feq_kernel(const StepConst<T> c, const Geom g, const double* __restrict__ rho,
                                 const double* __restrict__ ux, const double* __restrict__ uy,
@@ -23,7 +24,7 @@ __global__ void init_feq_kernel(const StepConst<T> c, const Geom g, const double
         for (int q = 0; q < NQ; ++q) {
             const T v = Arith<T>::feq(c, s, q);
             store_with_images(a, g, q, ix, iy, v);
-            store_with_images(b, g, q, ix, iy, v);
+            if (b) store_with_images(b, g, q, ix, iy, v);
         }
     }
 }

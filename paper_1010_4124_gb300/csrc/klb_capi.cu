@@ -338,6 +338,19 @@ void klb_destroy(klb_t* h) {
     delete h;
 }
 
+// The device's view of a host array: the array itself when it is pinned
+// (page-locked and mapped, as cudaHostAlloc / cudaHostRegister make it; the
+// kernels then read or write it across the host link directly, with no
+// staging copy), else NULL.
+static void* device_view(const void* host) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 static int stage_fields(klb_t* h, const double* rho, const double* ux, const double* uy, const double* T,
                         int on_device, const double** d) {
     const size_t n = (size_t)h->g.nx * h->g.ny;
@@ -346,6 +359,8 @@ static int stage_fields(klb_t* h, const double* rho, const double* ux, const dou
         if (!src[i]) return fail(h, KLB_E_INVAL, "NULL field pointer");
         if (on_device) {
             d[i] = src[i];
+        } else if (const void* v = device_view(src[i])) {
+            d[i] = (const double*)v;
         } else {
             CK(h, cudaMemcpyAsync(h->fields_dev + i * n, src[i], n * sizeof(double), cudaMemcpyHostToDevice,
                                   h->stream));
@@ -363,15 +378,16 @@ int klb_init_fields(klb_t* h, const double* rho, const double* ux, const double*
     int r = stage_fields(h, rho, ux, uy, T, on_device, d);
     if (r != KLB_OK) return r;
     cudaError_t e;
+    // the state goes to buffer 0 only: the first step writes every node and
+    // ghost image of buffer 1 (the fixed-equilibrium ghosts, which steps never
+    // write, go to both)
     if (h->p.precision == KLB_FP64) {
-        e = launch_init_feq<double>(h->cd, h->g, d[0], d[1], d[2], d[3], (double*)h->buf[0], (double*)h->buf[1],
-                                    h->stream);
+        e = launch_init_feq<double>(h->cd, h->g, d[0], d[1], d[2], d[3], (double*)h->buf[0], nullptr, h->stream);
         if (e == cudaSuccess)
             e = launch_fixed_ghosts<double>(h->cd, h->g, d[0], d[1], d[2], d[3], (double*)h->buf[0],
                                             (double*)h->buf[1], h->stream);
     } else {
-        e = launch_init_feq<float>(h->cf, h->g, d[0], d[1], d[2], d[3], (float*)h->buf[0], (float*)h->buf[1],
-                                   h->stream);
+        e = launch_init_feq<float>(h->cf, h->g, d[0], d[1], d[2], d[3], (float*)h->buf[0], nullptr, h->stream);
         if (e == cudaSuccess)
             e = launch_fixed_ghosts<float>(h->cf, h->g, d[0], d[1], d[2], d[3], (float*)h->buf[0],
                                            (float*)h->buf[1], h->stream);
@@ -564,7 +580,12 @@ int klb_moments(klb_t* h, double* rho, double* ux, double* uy, double* T, int on
     const size_t n = (size_t)h->g.nx * h->g.ny;
     double* dst[4] = {rho, ux, uy, T};
     double* d[4];
-    for (int i = 0; i < 4; ++i) d[i] = on_device ? dst[i] : (dst[i] ? h->fields_dev + i * n : nullptr);
+    bool direct[4];  // host outputs the kernel writes directly (pinned, mapped)
+    for (int i = 0; i < 4; ++i) {
+        void* v = (!on_device && dst[i]) ? device_view(dst[i]) : nullptr;
+        direct[i] = v != nullptr;
+        d[i] = on_device ? dst[i] : (v ? (double*)v : (dst[i] ? h->fields_dev + i * n : nullptr));
+    }
     cudaError_t e = h->p.precision == KLB_FP64
                         ? launch_fields<double>(h->cd, h->g, (const double*)h->buf[h->cur], d[0], d[1], d[2], d[3],
                                                 h->stream)
@@ -574,7 +595,8 @@ int klb_moments(klb_t* h, double* rho, double* ux, double* uy, double* T, int on
     h->launches += 1;
     if (!on_device)
         for (int i = 0; i < 4; ++i)
-            if (dst[i]) CK(h, cudaMemcpyAsync(dst[i], d[i], n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+            if (dst[i] && !direct[i])
+                CK(h, cudaMemcpyAsync(dst[i], d[i], n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     return klb_sync(h);
 }
 
