@@ -237,50 +237,13 @@ __device__ __forceinline__ int2 tile_divmod(int t, int d, float inv_d) {
     }
     return make_int2(q, r);
 }
-// The order in which a grid's tile rows are walked.  The persistent CTAs take
-// tiles t, t + G, ... (G CTAs), so tiles run in waves of G consecutive tiles,
-// which keeps the concurrent loads in contiguous row bands.  A wave spans
-// about G / tiles_x tile rows; walked in plain order, a tile and its
-// vertical neighbour would usually run in the same wave and both fetch their
-// shared halo rows from DRAM.  So the tile rows are split into m bands (m one
-// more than the rows of a wave, at most the rows of the grid) and walked
-// round-robin over the bands: walk row i is row k of band j (i = k m + j,
-// bands of base or base + 1 rows), and vertically neighbouring tiles fall in
-// different waves, the later one finding the halo rows in L2.
-struct TileWalk {
-    int tiles_x;
-    float inv_tx;  // correctly rounded 1 / tiles_x
-    int m, base, rem;
-    float inv_m;
-};
 template <int TY>
-__device__ __forceinline__ TileWalk tile_walk(int tiles_x, int ny, int G) {
-    TileWalk w;
-    w.tiles_x = tiles_x;
-    w.inv_tx = __frcp_rn((float)tiles_x);
-    const int rows = (ny + TY - 1) / TY;
-    const int m = (G + tiles_x - 1) / tiles_x + 1;
-    w.m = m < rows ? m : rows;
-    w.base = rows / w.m;
-    w.rem = rows - w.base * w.m;
-    w.inv_m = __frcp_rn((float)w.m);
-    return w;
-}
-template <int TY>
-__device__ __forceinline__ TileInfo tile_info(int t, const TileWalk& w) {
+__device__ __forceinline__ TileInfo tile_info(int t, int tiles_x, float inv_tx) {
     TileInfo ti;
-    const int2 qr = tile_divmod(t, w.tiles_x, w.inv_tx);  // (walk row, tile column)
+    const int2 qr = tile_divmod(t, tiles_x, inv_tx);
     const int tx = qr.y;
-    int row;
-    if (qr.x < w.base * w.m) {  // round k of all bands: band j's row k
-        const int2 kj = tile_divmod(qr.x, w.m, w.inv_m);
-        row = kj.y * w.base + (kj.y < w.rem ? kj.y : w.rem) + kj.x;
-    } else {  // the last round: the last row of each of the first rem bands
-        const int j = qr.x - w.base * w.m;
-        row = j * (w.base + 1) + w.base;
-    }
     ti.x0 = v3::TW * tx - GX;  // interior column of lane 0
-    ti.y0 = row * TY;
+    ti.y0 = qr.x * TY;
     ti.bxa = v3::TW * tx - 4;  // array column of the box start (16-byte aligned; -4 reads zeros)
     return ti;
 }
@@ -332,7 +295,7 @@ __global__ void __launch_bounds__(32 * TY, 16 / TY) step_f32_kernel(const __grid
         const int inst = MULTI ? find_inst(first, ninst, t) : 0;
         if (MULTI) tile_inst[b] = inst;
         const InstDesc* D = descs + inst;
-        const TileInfo ti = tile_info<TY>(t - D->first_tile, tile_walk<TY>(D->tiles_x, D->g.ny, gridDim.x));
+        const TileInfo ti = tile_info<TY>(t - D->first_tile, D->tiles_x, __frcp_rn((float)D->tiles_x));
         const uint32_t bar = smem_u32(&full[b]);
         tensormap_acquire(&D->map);
         mbar_arrive_expect_tx(bar, (uint32_t)(sizeof(float) * S::BOX_FLOATS));
@@ -353,8 +316,8 @@ __global__ void __launch_bounds__(32 * TY, 16 / TY) step_f32_kernel(const __grid
     const bool diag = diag_partials != nullptr;
     // fields of the instance of the current tile, read from global memory
     // only when the instance changes (tiles of one instance are contiguous)
-    int cur = -1, first_t = 0;
-    TileWalk walk{};
+    int cur = -1, first_t = 0, tiles_x = 1;
+    float inv_tx = 1.f;
     Geom g{};
     float* out = nullptr;
     int k = 0;  // local tile counter: buffer k & 1, phase (k >> 1) & 1
@@ -378,11 +341,12 @@ __global__ void __launch_bounds__(32 * TY, 16 / TY) step_f32_kernel(const __grid
             g = D->g;
             out = D->out;
             first_t = D->first_tile;
-            walk = tile_walk<TY>(D->tiles_x, g.ny, gridDim.x);
+            tiles_x = D->tiles_x;
+            inv_tx = __frcp_rn((float)tiles_x);
             cur = inst;
         }
         const float* tile = buf + b * S::BUF_FLOATS;
-        const TileInfo ti = tile_info<TY>(t - first_t, walk);
+        const TileInfo ti = tile_info<TY>(t - first_t, tiles_x, inv_tx);
         const int ix = ti.x0 + lane, iy = ti.y0 + ty;
         const int s = lane + 4;  // smem column of the node
         const int r = ty + 3;    // smem row of the node
@@ -452,19 +416,19 @@ __global__ void __launch_bounds__(32 * TY, 16 / TY) step_f32_kernel(const __grid
     if (diag) diag_block_reduce<S::NT>(acc, diag_partials + 8ll * blockIdx.x);
 }
 
-// Diagnostics of a state with the same tiles, per-CTA tile order (tile_walk
-// with the same number of CTAs) and block reduction as the fused path inside
-// the step kernel, so that both give the same bits: CTA `cta` of `ncta` takes
-// tiles cta, cta + ncta, ... and writes one partial record.
+// Diagnostics of a state with the same tiles, per-CTA tile order and block
+// reduction as the fused path inside the step kernel, so that both give the
+// same bits: CTA `cta` of `ncta` takes tiles cta, cta + ncta, ... and writes
+// one partial record.
 template <int TY>
 __device__ __forceinline__ void diag_cta(const StepConst<float>& c, const Geom& g, int tiles_x, int ntiles,
                                          const float* __restrict__ f, double* __restrict__ partial, int cta,
                                          int ncta) {
     const int tid = threadIdx.x, ty = tid >> 5, lane = tid & 31;
-    const TileWalk walk = tile_walk<TY>(tiles_x, g.ny, ncta);
+    const float inv_tx = __frcp_rn((float)tiles_x);
     // the node of tile t for this thread, its activity and its 19 values
     auto load = [&](int t, float fl[NQ]) {
-        const TileInfo ti = tile_info<TY>(t, walk);
+        const TileInfo ti = tile_info<TY>(t, tiles_x, inv_tx);
         const int ix = ti.x0 + lane, iy = ti.y0 + ty;
         const bool active = ix >= 0 && ix < g.nx && iy < g.ny;
 #pragma unroll

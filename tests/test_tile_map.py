@@ -59,34 +59,3 @@ def test_fails_above_the_admitted_range():
     t = np.arange((1 << 26) - 3000, 1 << 26, dtype=np.int64)
     q, r = split(t, d)
     assert np.any(q != t // d)
-
-
-def walk_rows(rows, m):
-    """The FP32 kernels' order of tile rows (tile_walk / tile_info in
-    klb_step_f32.cuh), transcribed: walk position i -> tile row, round-robin
-    over m bands of base or base + 1 rows."""
-    m = min(m, rows)
-    base, rem = rows // m, rows % m
-    out = []
-    for i in range(rows):
-        if i < base * m:
-            k, j = divmod(i, m)
-            out.append(j * base + min(j, rem) + k)
-        else:
-            j = i - base * m
-            out.append(j * (base + 1) + base)
-    return out
-
-
-def test_band_walk_visits_every_row_once_and_separates_neighbours():
-    for rows in list(range(1, 70)) + [256, 257, 512, 1000]:
-        for m in (1, 2, 3, 4, 7, 11, 64, 300):
-            w = walk_rows(rows, m)
-            assert sorted(w) == list(range(rows)), (rows, m)
-            mm = min(m, rows)
-            if mm >= 2 and rows // mm >= 2:
-                # rows next to each other in the grid are at least a band's
-                # width apart in the walk (except at the bands' seams)
-                pos = {r: i for i, r in enumerate(w)}
-                close = sum(1 for r in range(rows - 1) if abs(pos[r] - pos[r + 1]) < mm - 1)
-                assert close <= mm, (rows, m, close)
