@@ -61,3 +61,24 @@ def test_slabs_refuse_thin_slabs_and_halo_domains():
         klb.KlbSlabs.from_problem(pb, 3, "fp32")  # slabs of 2-3 rows: shallower than the ghost layer
     with pytest.raises(klb.KlbError):
         klb.KlbSlabs.from_problem(pb.with_(bc_y=("halo", "halo")), 2, "fp32")
+
+
+def test_slabs_with_device_fields_and_output():
+    # fields and the assembled distribution as torch device tensors (each slab
+    # takes its rows of the fields by pointer offset; the distribution is
+    # gathered on the device)
+    torch = pytest.importorskip("torch")
+    pb = _problem(48, 40, "outflow", 12)
+    fields = [np.ascontiguousarray(a) for a in inputs.smooth_random_fields(pb.nx, pb.ny, seed=7, amp=0.08)]
+    dev = [torch.from_numpy(a).cuda() for a in fields]
+    with klb.KlbSlabs.from_problem(pb, 2, "fp32") as s:
+        s.init_fields(*dev)
+        s.step(pb.steps)
+        out = torch.empty((19, pb.ny, pb.nx), dtype=torch.float64, device="cuda")
+        s.get_f(out)
+        host = s.get_f()
+    with klb.Klb.from_problem(pb, "fp32") as h:
+        h.init_fields(*fields)
+        h.step(pb.steps)
+        ref = h.get_f()
+    assert np.array_equal(out.cpu().numpy(), ref) and np.array_equal(host, ref)
