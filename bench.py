@@ -388,7 +388,7 @@ def sweep_measure(steps: int, torch):
         h = klb.Klb.from_problem(pb, precision="fp32", stream=stream.cuda_stream)
         h.variant = variant
         h.init_fields(*fl)
-        h.step(3)
+        h.step(80)  # warm-up: also captures the step graph the timed run replays
         hs.append(h)
     torch.cuda.synchronize()
     e0.record(stream)
@@ -467,7 +467,7 @@ def adjoint_measure(prec: str, steps: int, torch):
     if prec == "fp32":
         h.variant = pick_variant(h, stream, torch)
         h.init_fields(*dev)
-    h.step(20)
+    h.step(80)  # warm-up: also captures the step graph the timed run replays
     h.sync()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)

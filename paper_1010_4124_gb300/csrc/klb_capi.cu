@@ -313,6 +313,14 @@ int klb_create(const klb_params* pin, klb_t** out) {
             g_create_error = h->err;
             return cleanup(r);
         }
+        // graph replay of the step loop (FP32 WENO5): the kernel attributes are
+        // set here, outside any capture; runs of at least 64 steps, a multiple
+        // of the sampling period and even (the parity comes back)
+        if (p.scheme == KLB_WENO5 && fdlb::prepare_f32_kernels() == cudaSuccess) {
+            const int64_t unit = p.sample_every > 0 ? (p.sample_every % 2 == 0 ? p.sample_every : 2ll * p.sample_every)
+                                                    : 2;
+            if (unit <= 512) h->graph_steps = (int)(unit * ((64 + unit - 1) / unit));
+        }
     }
     if (cudaDeviceSynchronize() != cudaSuccess) {
         fail(nullptr, KLB_E_CUDA, "device synchronisation after allocation failed");
@@ -325,6 +333,7 @@ int klb_create(const klb_params* pin, klb_t** out) {
 void klb_destroy(klb_t* h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
+    fdlb::handle_drop_graphs(h);
     for (int i = 0; i < 2; ++i)
         if (h->buf[i]) cudaFree(h->buf[i]);
     if (h->fields_dev) cudaFree(h->fields_dev);
@@ -531,6 +540,49 @@ static int one_step(klb_t* h) {
     return KLB_OK;
 }
 
+void fdlb::handle_drop_graphs(klb_t* h) {
+    for (int p = 0; p < 2; ++p)
+        for (int d = 0; d < 2; ++d)
+            if (h->graph[p][d]) {
+                cudaGraphExecDestroy(h->graph[p][d]);
+                h->graph[p][d] = nullptr;
+            }
+}
+
+// capture graph_steps steps from the handle's present parity and sampling
+// state (a step count that is a multiple of the sampling period): the
+// capture records the launches only, so the bookkeeping is restored after it
+static int build_step_graph(klb_t* h) {
+    const int p = h->cur, d = h->pending_sample ? 1 : 0;
+    const int cur = h->cur;
+    const int64_t steps = h->steps, launches = h->launches;
+    const bool pending = h->pending_sample;
+    cudaGraph_t g = nullptr;
+    CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    int r = KLB_OK;
+    for (int s = 0; s < h->graph_steps && r == KLB_OK; ++s) r = one_step(h);
+    cudaError_t ec = cudaStreamEndCapture(h->stream, &g);
+    h->graph_launches[p][d] = h->launches - launches;
+    h->cur = cur;
+    h->steps = steps;
+    h->launches = launches;
+    h->pending_sample = pending;
+    if (r != KLB_OK || ec != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        h->use_graph = false;  // step one launch at a time from now on
+        cudaGetLastError();
+        return r != KLB_OK ? r : KLB_OK;
+    }
+    cudaError_t ei = cudaGraphInstantiate(&h->graph[p][d], g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+        h->graph[p][d] = nullptr;
+        h->use_graph = false;
+        cudaGetLastError();
+    }
+    return KLB_OK;
+}
+
 extern "C" {
 
 int klb_step(klb_t* h, int64_t n) {
@@ -539,9 +591,35 @@ int klb_step(klb_t* h, int64_t n) {
     if (n < 0) return fail(h, KLB_E_INVAL, "negative step count");
     if (!h->initialized) return fail(h, KLB_E_STATE, "klb_step before klb_init_fields");
     if (h->broken) return fail(h, KLB_E_STATE, "the handle's tile shape could not be restored (klb_set_variant)");
-    for (int64_t s = 0; s < n; ++s) {
+    const int se = h->p.sample_every;
+    while (n > 0) {
+        // FP32 WENO5 runs of graph_steps steps, starting at a sampling point,
+        // are replayed from a CUDA graph (small grids are bound by launch
+        // latency); the graph's steps leave the parity where it was and the
+        // next sample due, exactly as stepping one launch at a time would
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        const bool graphable = h->use_graph && h->graph_steps > 0 && n >= h->graph_steps && h->inject == 0 &&
+                               (se == 0 || h->steps % se == 0) &&
+                               cudaStreamIsCapturing(h->stream, &cs) == cudaSuccess &&
+                               cs == cudaStreamCaptureStatusNone;
+        if (graphable) {
+            const int p = h->cur, d = h->pending_sample ? 1 : 0;
+            if (!h->graph[p][d]) {
+                int r = build_step_graph(h);
+                if (r != KLB_OK) return r;
+            }
+            if (h->graph[p][d]) {
+                CK(h, cudaGraphLaunch(h->graph[p][d], h->stream));
+                h->launches += h->graph_launches[p][d];
+                h->steps += h->graph_steps;
+                h->pending_sample = se > 0;  // graph_steps is a multiple of the sampling period
+                n -= h->graph_steps;
+                continue;
+            }
+        }
         int r = one_step(h);
         if (r != KLB_OK) return r;
+        n -= 1;
     }
     return KLB_OK;
 }
@@ -646,6 +724,7 @@ int klb_debug_inject_wait_timeout(klb_t* h, int64_t polls) {
     if (!h || polls < 0) return KLB_E_INVAL;
     h->inject = polls > 0 ? 1 : 0;
     h->spin_limit = polls > 0 ? polls : kDefaultSpin;
+    fdlb::handle_drop_graphs(h);  // the wait budget is a launch parameter
     return KLB_OK;
 }
 
@@ -686,6 +765,7 @@ int klb_set_variant(klb_t* h, int variant) {
         h->err = msg;
         return code;
     };
+    fdlb::handle_drop_graphs(h);  // their launches name the old tile shape
     h->variant = variant;
     for (int i = 0; i < 2; ++i) {
         int r = make_map(h, h->buf[i], &h->map[i]);

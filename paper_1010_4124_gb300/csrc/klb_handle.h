@@ -43,6 +43,12 @@ struct klb {  // state of one grid
     InstDesc* descs_dev = nullptr;   // FP32: descriptors of the state in buf[0] / buf[1] (2 entries)
     int ntiles = 0;                  // FP32: tiles of one launch (current variant)
     long long* nsamp_dev = nullptr;  // samples taken (device counter; the finalize kernel advances it)
+    // FP32 WENO5: runs of graph_steps steps replayed from CUDA graphs, by
+    // starting parity and whether the starting state's sample is due
+    int graph_steps = 0;
+    cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    int64_t graph_launches[2][2] = {{0, 0}, {0, 0}};
+    bool use_graph = true;
     std::string err;
 };
 
@@ -62,6 +68,7 @@ void step_constants(const klb_params& p, StepConst<double>& c);
 // helpers of klb_capi.cu used by the batch engine
 int handle_fail(klb_t* h, int code, const std::string& msg);
 int handle_upload_descs(klb_t* h);  // (re)build the FP32 descriptors and the tile count
+void handle_drop_graphs(klb_t* h);  // forget the captured step graphs (their launches changed)
 // TMA map of a state buffer of the handle's layout (x: pitch, y: rows with
 // ghosts, z: 19 planes) with a box of bx x by x bz elements
 int encode_state_map(klb_t* h, const void* base, unsigned bx, unsigned by, unsigned bz, CUtensorMap* map);

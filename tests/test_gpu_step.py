@@ -519,3 +519,29 @@ def test_fp32_one_step_parity_every_size(nx, ny, bcx, bcy):
             got.append(h.get_f())
     assert np.array_equal(got[0], got[1])
     assert rel_err_global(got[0], ref) <= 2e-6
+
+
+@pytest.mark.parametrize("sample_every", [0, 10, 7])
+def test_graph_replayed_steps_equal_single_launches(sample_every):
+    # klb_step replays runs of steps from a CUDA graph (FP32 WENO5, runs of at
+    # least 64 steps starting at a sampling point); stepping one call per step
+    # never does.  Both must give the same states and diagnostics, bit for bit,
+    # including runs that start off a sampling point and a ragged remainder.
+    pb = inputs.khi(96, 80, 0, sample_every=sample_every)
+    fields = inputs.fields(pb)
+    out = []
+    for graphs in (True, False):
+        with gpu_handle(pb, "fp32", sample_every=sample_every) as h:
+            h.init_fields(*fields)
+            if graphs:
+                h.step(3)
+                h.step(200)
+                h.step(157)
+            else:
+                for _ in range(360):
+                    h.step(1)
+            assert h.step_count == 360
+            out.append((h.get_f(), h.diagnostics() if sample_every else None))
+    assert np.array_equal(out[0][0], out[1][0])
+    if sample_every:
+        assert np.array_equal(out[0][1], out[1][1])
