@@ -46,6 +46,18 @@ struct klb_adj {
     double* dense = nullptr;       // staging for host / dense arrays (19 * nx * ny)
     std::deque<AdjMap> maps;       // TMA maps of the buffers above (stable addresses)
     InstDesc* rdescs = nullptr;    // FP32: step descriptors of the recomputation chains (device)
+    int rdescs_variant = -1;       // the tile shape they were built for
+    double* coef_dev = nullptr;    // the objective's weight of each reverse step (nsteps)
+    std::vector<double> coef_host;
+    bool use_graph = true;         // forward and reverse sweep replayed from CUDA graphs
+    cudaGraphExec_t sweep_graph = nullptr;
+    int64_t sweep_launches = 0;
+    int lam_final = 0;             // the lambda buffer that holds lambda^0 after the sweep
+    cudaGraphExec_t fwd_graph = nullptr;  // checkpoints and steps of the forward run
+    int64_t fwd_launches = 0;
+    int fwd_cur = 0;               // the grid's bookkeeping after the forward run
+    int64_t fwd_steps = 0;
+    bool fwd_pending = false;
     std::vector<double> K;         // K_s of the forward run
     double ke = 0, gamma = 0;
     bool forward_done = false;
@@ -105,7 +117,7 @@ static void launch_fold(const Geom& g, T* lam, cudaStream_t s) {
 }
 
 template <typename T>
-static int vjp_step(klb_adj_t* a, const void* f, void* lam_in, void* lam_out, double coef) {
+static int vjp_step(klb_adj_t* a, const void* f, void* lam_in, void* lam_out, int64_t n) {
     klb_t* h = a->h;
     const StepConst<T>& c = *reinterpret_cast<const StepConst<T>*>(sizeof(T) == 8 ? (const void*)&h->cd
                                                                                    : (const void*)&h->cf);
@@ -123,7 +135,7 @@ static int vjp_step(klb_adj_t* a, const void* f, void* lam_in, void* lam_out, do
                                                                  h->spin_limit);
     const long long tiles = (long long)A::tiles_x(g.nx) * A::tiles_y(g.ny);
     adj_tile_kernel<T, adj_rows<T>()><<<dim3((unsigned)tiles, NQ), 32 * adj_rows<T>(), 0, h->stream>>>(
-        *fmap, *lmap, c, g, (const T*)a->Nb, T(coef), (T*)lam_out, h->err_dev, h->spin_limit);
+        *fmap, *lmap, c, g, (const T*)a->Nb, a->coef_dev, (int)n, (T*)lam_out, h->err_dev, h->spin_limit);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return afail(a, KLB_E_CUDA, std::string("adjoint kernels: ") + cudaGetErrorString(e));
     h->launches += 3;
@@ -141,9 +153,9 @@ static int fold(klb_adj_t* a, void* lam) {
     return KLB_OK;
 }
 
-static int vjp(klb_adj_t* a, const void* f, void* lam_in, void* lam_out, double coef) {
-    return a->h->p.precision == KLB_FP64 ? vjp_step<double>(a, f, lam_in, lam_out, coef)
-                                         : vjp_step<float>(a, f, lam_in, lam_out, coef);
+static int vjp(klb_adj_t* a, const void* f, void* lam_in, void* lam_out, int64_t n) {
+    return a->h->p.precision == KLB_FP64 ? vjp_step<double>(a, f, lam_in, lam_out, n)
+                                         : vjp_step<float>(a, f, lam_in, lam_out, n);
 }
 
 template <typename T>
@@ -213,7 +225,11 @@ static int step_into(klb_adj_t* a, const void* in, void* out, int desc_index) {
 // seg[k] into seg[k + 1]
 static int upload_recompute_descs(klb_adj_t* a) {
     klb_t* h = a->h;
-    if (h->p.precision != KLB_FP32 || a->seg.empty()) return KLB_OK;
+    if (h->p.precision != KLB_FP32 || a->seg.empty() || a->rdescs_variant == h->variant) return KLB_OK;
+    if (a->sweep_graph) {  // its step launches name the old tile shape
+        cudaGraphExecDestroy(a->sweep_graph);
+        a->sweep_graph = nullptr;
+    }
     unsigned bx, by, bz;
     f32_box(h->variant, &bx, &by, &bz);
     int tiles_x, ntiles;
@@ -231,17 +247,18 @@ static int upload_recompute_descs(klb_adj_t* a) {
     }
     ACK(a, cudaMemcpyAsync(a->rdescs, d.data(), d.size() * sizeof(InstDesc), cudaMemcpyHostToDevice, h->stream));
     ACK(a, cudaStreamSynchronize(h->stream));  // the host vector goes out of scope
+    a->rdescs_variant = h->variant;
     return KLB_OK;
 }
 
-// the reverse sweep from lam[cur_l] = lambda^N down to lambda^0; with
-// objective sources when `sources` is set (g_ke, g_gamma)
-static int reverse(klb_adj_t* a, bool sources, double g_ke, double g_gamma, int* lam_cur) {
-    int lc = *lam_cur;
-    int r = upload_recompute_descs(a);
-    if (r != KLB_OK) return r;
+// The launches of the reverse sweep from lam[0] = lambda^N down to lambda^0
+// (segments in reverse order: the recomputation of a segment's states, then
+// its reverse steps; finally the fold of lambda^0's ghost sums).  The
+// objective's weights are read from coef_dev, so the sequence is the same for
+// every call: it is captured into a CUDA graph once and replayed.
+static int sweep_launches(klb_adj_t* a) {
+    int lc = 0, r = KLB_OK;
     for (int s = a->nck - 1; s >= 0; --s) {
-        fdlb::NvtxRange trace_("klb_adjoint segment");
         const int64_t n0 = (int64_t)s * a->ckpt;
         const int64_t n1 = std::min<int64_t>(n0 + a->ckpt, a->nsteps);
         const int len = (int)(n1 - n0);
@@ -255,16 +272,56 @@ static int reverse(klb_adj_t* a, bool sources, double g_ke, double g_gamma, int*
             states[k] = a->seg[k - 1];
         }
         for (int64_t n = n1 - 1; n >= n0; --n) {
-            double coef = 0.0;
-            const int si = sample_of(a, n);
-            if (sources && si >= 0) coef = dL_dK(a, si, g_ke, g_gamma);
-            r = vjp(a, states[n - n0], a->lam[lc], a->lam[1 - lc], coef);
+            r = vjp(a, states[n - n0], a->lam[lc], a->lam[1 - lc], n);
             if (r != KLB_OK) return r;
             lc = 1 - lc;
         }
     }
-    *lam_cur = lc;
+    a->lam_final = lc;
     return a->h->p.precision == KLB_FP64 ? fold<double>(a, a->lam[lc]) : fold<float>(a, a->lam[lc]);
+}
+
+// the reverse sweep; with objective sources (g_ke, g_gamma) when `sources` is
+// set; returns the buffer of lambda^0 in *lam_cur
+static int reverse(klb_adj_t* a, bool sources, double g_ke, double g_gamma, int* lam_cur) {
+    klb_t* h = a->h;
+    int r = upload_recompute_descs(a);
+    if (r != KLB_OK) return r;
+    // the objective's weight of each reverse step (the samples it enters)
+    for (int64_t n = 0; n < a->nsteps; ++n) {
+        const int si = sample_of(a, n);
+        a->coef_host[n] = (sources && si >= 0) ? dL_dK(a, si, g_ke, g_gamma) : 0.0;
+    }
+    ACK(a, cudaMemcpyAsync(a->coef_dev, a->coef_host.data(), sizeof(double) * a->nsteps, cudaMemcpyHostToDevice,
+                           h->stream));
+    if (!a->sweep_graph && a->use_graph) {
+        const int64_t l0 = h->launches;
+        cudaGraph_t g = nullptr;
+        ACK(a, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        r = sweep_launches(a);
+        cudaError_t ec = cudaStreamEndCapture(h->stream, &g);
+        a->sweep_launches = h->launches - l0;
+        h->launches = l0;
+        if (r != KLB_OK) {
+            if (g) cudaGraphDestroy(g);
+            return r;
+        }
+        if (ec != cudaSuccess || cudaGraphInstantiate(&a->sweep_graph, g, 0) != cudaSuccess) {
+            a->sweep_graph = nullptr;
+            a->use_graph = false;  // launch the sweep eagerly from now on
+            cudaGetLastError();
+        }
+        if (g) cudaGraphDestroy(g);
+    }
+    if (a->sweep_graph) {
+        ACK(a, cudaGraphLaunch(a->sweep_graph, h->stream));
+        h->launches += a->sweep_launches;
+    } else {
+        r = sweep_launches(a);
+        if (r != KLB_OK) return r;
+    }
+    *lam_cur = a->lam_final;
+    return KLB_OK;
 }
 
 template <typename T>
@@ -307,6 +364,9 @@ int klb_adjoint_create(const klb_params* p, int64_t nsteps, int32_t checkpoint_e
         return afail(nullptr, r, std::string("forward grid: ") + klb_last_error(nullptr));
     }
     klb_t* h = a->h;  // an FP32 grid starts with the tile shape faster for its size
+    // graph replay of the forward run and the reverse sweep (FP32: the step
+    // kernels' attributes are set at creation, outside any capture)
+    a->use_graph = h->p.precision == KLB_FP32;
     const size_t sb = state_bytes(h);
     const size_t nn = (size_t)h->g.nx * h->g.ny;
     bool ok = true;
@@ -317,6 +377,8 @@ int klb_adjoint_create(const klb_params* p, int64_t nsteps, int32_t checkpoint_e
     for (int k = 0; k < 2 && ok; ++k) ok = cudaMalloc(&a->lam[k], sb) == cudaSuccess;
     ok = ok && cudaMalloc(&a->Nb, h->esize * 5 * nn) == cudaSuccess;
     ok = ok && cudaMalloc(&a->rdescs, sizeof(InstDesc) * (a->nck + a->seg.size() + 1)) == cudaSuccess;
+    ok = ok && cudaMalloc(&a->coef_dev, sizeof(double) * nsteps) == cudaSuccess;
+    a->coef_host.assign(nsteps, 0.0);
     ok = ok && cudaMalloc(&a->fields, sizeof(double) * 4 * nn) == cudaSuccess;
     ok = ok && cudaMalloc(&a->dense, sizeof(double) * NQ * nn) == cudaSuccess;
     if (!ok) {
@@ -340,6 +402,9 @@ void klb_adjoint_destroy(klb_adj_t* a) {
         if (a->lam[k]) cudaFree(a->lam[k]);
     if (a->Nb) cudaFree(a->Nb);
     if (a->rdescs) cudaFree(a->rdescs);
+    if (a->coef_dev) cudaFree(a->coef_dev);
+    if (a->sweep_graph) cudaGraphExecDestroy(a->sweep_graph);
+    if (a->fwd_graph) cudaGraphExecDestroy(a->fwd_graph);
     if (a->fields) cudaFree(a->fields);
     if (a->dense) cudaFree(a->dense);
     klb_destroy(a->h);
@@ -360,11 +425,55 @@ int klb_adjoint_forward(klb_adj_t* a, const double* rho, const double* ux, const
                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
     int r = klb_init_fields(h, a->fields, a->fields + nn, a->fields + 2 * nn, a->fields + 3 * nn, 1);
     if (r != KLB_OK) return afail(a, r, h->err);
-    for (int s = 0; s < a->nck; ++s) {
-        ACK(a, cudaMemcpyAsync(a->ck[s], h->buf[h->cur], state_bytes(h), cudaMemcpyDeviceToDevice, h->stream));
-        const int64_t n = std::min<int64_t>(a->ckpt, a->nsteps - (int64_t)s * a->ckpt);
-        r = klb_step(h, n);
-        if (r != KLB_OK) return afail(a, r, h->err);
+    // the checkpoint copies and steps of the run: the same launches for every
+    // initial state, captured into a CUDA graph once and replayed
+    auto run = [&]() -> int {
+        for (int s = 0; s < a->nck; ++s) {
+            ACK(a, cudaMemcpyAsync(a->ck[s], h->buf[h->cur], state_bytes(h), cudaMemcpyDeviceToDevice, h->stream));
+            const int64_t n = std::min<int64_t>(a->ckpt, a->nsteps - (int64_t)s * a->ckpt);
+            int rr = klb_step(h, n);
+            if (rr != KLB_OK) return afail(a, rr, h->err);
+        }
+        return KLB_OK;
+    };
+    if (a->use_graph && !a->fwd_graph) {
+        const int cur = h->cur;
+        const int64_t steps = h->steps, l0 = h->launches;
+        const bool pending = h->pending_sample;
+        cudaGraph_t g = nullptr;
+        ACK(a, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        r = run();
+        cudaError_t ec = cudaStreamEndCapture(h->stream, &g);
+        // the capture recorded the launches; the bookkeeping it advanced is the
+        // state every replay ends in
+        a->fwd_cur = h->cur;
+        a->fwd_steps = h->steps;
+        a->fwd_pending = h->pending_sample;
+        a->fwd_launches = h->launches - l0;
+        h->cur = cur;
+        h->steps = steps;
+        h->launches = l0;
+        h->pending_sample = pending;
+        if (r != KLB_OK) {
+            if (g) cudaGraphDestroy(g);
+            return r;
+        }
+        if (ec != cudaSuccess || cudaGraphInstantiate(&a->fwd_graph, g, 0) != cudaSuccess) {
+            a->fwd_graph = nullptr;
+            a->use_graph = false;
+            cudaGetLastError();
+        }
+        if (g) cudaGraphDestroy(g);
+    }
+    if (a->fwd_graph) {
+        ACK(a, cudaGraphLaunch(a->fwd_graph, h->stream));
+        h->cur = a->fwd_cur;
+        h->steps = a->fwd_steps;
+        h->pending_sample = a->fwd_pending;
+        h->launches += a->fwd_launches;
+    } else {
+        r = run();
+        if (r != KLB_OK) return r;
     }
     const int64_t M = a->nsteps / h->p.sample_every + 1;
     std::vector<double> d((size_t)M * 7);

@@ -288,6 +288,7 @@ __global__ void adj_fold_kernel(const Geom g, T* __restrict__ lam, int nbx, int 
         const int m = image_cells(g, i, j, cell);
         const long long at = (long long)(j + GY) * g.px + (i + GX);
         const long long lim = (NQ - q) * g.plane;  // the cells of planes q .. 18 from L
+        (void)lim;  // read by the guards of the bounds-checked build only
         T v = KLB_LOAD(L, at, lim, T(0));
         for (int k = 0; k < m; ++k) v += KLB_LOAD(L, cell[k], lim, T(0));
         for (int k = 0; k < m; ++k) {
@@ -497,7 +498,7 @@ __device__ __forceinline__ void adj_tile_body(const StepConst<T>& c, const Geom&
     }
 }
 
-// One CTA: velocity q = blockIdx.y on tile blockIdx.x.  f^n_q (halo 5: the
+// One CTA: velocity q = blockIdx.y on tile blockIdx.x, reverse step nstep.  f^n_q (halo 5: the
 // stencils of the faces within 3 of the tile) and lambda^{n+1}_q (halo 3: the
 // faces' mu) arrive by two TMA box loads (plain cp.async.bulk.tensor, no
 // multicast) on one mbarrier; a wait that runs out sets ERR_TIMEOUT.
@@ -507,8 +508,9 @@ template <typename T, int TY>
 __global__ void __launch_bounds__(32 * TY) adj_tile_kernel(const __grid_constant__ CUtensorMap fmap,
                                                            const __grid_constant__ CUtensorMap lmap,
                                                            const StepConst<T> c, const Geom g,
-                                                           const T* __restrict__ N, T coef, T* __restrict__ lam_out,
-                                                           int* __restrict__ err, long long spin_limit) {
+                                                           const T* __restrict__ N, const double* __restrict__ coefs,
+                                                           int nstep, T* __restrict__ lam_out, int* __restrict__ err,
+                                                           long long spin_limit) {
     using A = AdjTile<T, TY>;
     constexpr int TX = A::TX;
     static_assert(TY >= 7, "the remainder pass needs warps 0..4 and two more");
@@ -542,6 +544,9 @@ __global__ void __launch_bounds__(32 * TY) adj_tile_kernel(const __grid_constant
         return;
     }
     const int sx = sgn_x(q), sy = sgn_y(q);  // uniform across the CTA
+    // the objective's weight at this step (0 where no sample enters), read from
+    // device memory so that a captured sweep serves every objective
+    const T coef = T(coefs[nstep]);
 #define KLB_ADJ_BODY(SX, SY) adj_tile_body<T, TY, SX, SY>(c, g, q, x0, y0, fs, ls, gx, gy, N, coef, lam_out)
     if (sx == 0) KLB_ADJ_BODY(0, 0);
     else if (sx > 0 && sy > 0) KLB_ADJ_BODY(1, 1);
