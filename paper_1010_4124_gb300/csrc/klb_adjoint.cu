@@ -294,10 +294,14 @@ static int reverse(klb_adj_t* a, bool sources, double g_ke, double g_gamma, int*
     }
     ACK(a, cudaMemcpyAsync(a->coef_dev, a->coef_host.data(), sizeof(double) * a->nsteps, cudaMemcpyHostToDevice,
                            h->stream));
-    if (!a->sweep_graph && a->use_graph) {
+    if (!a->sweep_graph && a->use_graph &&
+        cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        a->use_graph = false;  // a stream that cannot be captured: launch eagerly
+    }
+    if (!a->sweep_graph && a->use_graph) {  // capturing
         const int64_t l0 = h->launches;
         cudaGraph_t g = nullptr;
-        ACK(a, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
         r = sweep_launches(a);
         cudaError_t ec = cudaStreamEndCapture(h->stream, &g);
         a->sweep_launches = h->launches - l0;
@@ -436,12 +440,16 @@ int klb_adjoint_forward(klb_adj_t* a, const double* rho, const double* ux, const
         }
         return KLB_OK;
     };
-    if (a->use_graph && !a->fwd_graph) {
+    if (a->use_graph && !a->fwd_graph &&
+        cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        a->use_graph = false;  // a stream that cannot be captured: launch eagerly
+    }
+    if (a->use_graph && !a->fwd_graph) {  // capturing
         const int cur = h->cur;
         const int64_t steps = h->steps, l0 = h->launches;
         const bool pending = h->pending_sample;
         cudaGraph_t g = nullptr;
-        ACK(a, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
         r = run();
         cudaError_t ec = cudaStreamEndCapture(h->stream, &g);
         // the capture recorded the launches; the bookkeeping it advanced is the

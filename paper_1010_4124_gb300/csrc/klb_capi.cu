@@ -558,7 +558,11 @@ static int build_step_graph(klb_t* h) {
     const int64_t steps = h->steps, launches = h->launches;
     const bool pending = h->pending_sample;
     cudaGraph_t g = nullptr;
-    CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        h->use_graph = false;  // a stream that cannot be captured: one launch per step
+        return KLB_OK;
+    }
     int r = KLB_OK;
     for (int s = 0; s < h->graph_steps && r == KLB_OK; ++s) r = one_step(h);
     cudaError_t ec = cudaStreamEndCapture(h->stream, &g);
