@@ -545,3 +545,30 @@ def test_graph_replayed_steps_equal_single_launches(sample_every):
     assert np.array_equal(out[0][0], out[1][0])
     if sample_every:
         assert np.array_equal(out[0][1], out[1][1])
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_pinned_host_fields_and_moments_equal_pageable(prec):
+    # pinned host arrays are read (init) and written (moments) by the kernels
+    # directly across the host link; pageable ones go through device staging:
+    # the same states and moments either way
+    torch = pytest.importorskip("torch")
+    pb = inputs.khi(90, 70, 15)
+    fields = [np.ascontiguousarray(a) for a in inputs.fields(pb)]
+    pinned = [torch.from_numpy(a.copy()).pin_memory() for a in fields]
+    out = []
+    for src in ("pageable", "pinned"):
+        with gpu_handle(pb, prec) as h:
+            h.init_fields(*(fields if src == "pageable" else [p.numpy() for p in pinned]))
+            h.step(pb.steps)
+            f = h.get_f()
+            if src == "pageable":
+                m = h.moments()
+            else:
+                m = tuple(torch.empty((pb.ny, pb.nx), dtype=torch.float64).pin_memory() for _ in range(4))
+                h.moments(tuple(t.numpy() for t in m))
+                m = tuple(t.numpy() for t in m)
+            out.append((f, [np.array(a) for a in m]))
+    assert np.array_equal(out[0][0], out[1][0])
+    for a, b in zip(out[0][1], out[1][1]):
+        assert np.array_equal(a, b)
