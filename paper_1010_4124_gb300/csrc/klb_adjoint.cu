@@ -58,6 +58,9 @@ struct klb_adj {
     int fwd_cur = 0;               // the grid's bookkeeping after the forward run
     int64_t fwd_steps = 0;
     bool fwd_pending = false;
+    int fwd_variant = -1;          // the grid's tile shape and wait budget the graphs were captured with
+    long long fwd_spin = 0;
+    long long sweep_spin = 0;
     std::vector<double> K;         // K_s of the forward run
     double ke = 0, gamma = 0;
     bool forward_done = false;
@@ -294,12 +297,17 @@ static int reverse(klb_adj_t* a, bool sources, double g_ke, double g_gamma, int*
     }
     ACK(a, cudaMemcpyAsync(a->coef_dev, a->coef_host.data(), sizeof(double) * a->nsteps, cudaMemcpyHostToDevice,
                            h->stream));
-    if (!a->sweep_graph && a->use_graph &&
+    if (a->sweep_graph && (a->sweep_spin != h->spin_limit || h->inject)) {  // stale wait budget
+        cudaGraphExecDestroy(a->sweep_graph);
+        a->sweep_graph = nullptr;
+    }
+    if (!a->sweep_graph && a->use_graph && !h->inject &&
         cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         cudaGetLastError();
         a->use_graph = false;  // a stream that cannot be captured: launch eagerly
     }
-    if (!a->sweep_graph && a->use_graph) {  // capturing
+    if (!a->sweep_graph && a->use_graph && !h->inject) {  // capturing
+        a->sweep_spin = h->spin_limit;
         const int64_t l0 = h->launches;
         cudaGraph_t g = nullptr;
         r = sweep_launches(a);
@@ -440,12 +448,19 @@ int klb_adjoint_forward(klb_adj_t* a, const double* rho, const double* ux, const
         }
         return KLB_OK;
     };
-    if (a->use_graph && !a->fwd_graph &&
+    // a graph captured for another tile shape or wait budget of the grid is stale
+    if (a->fwd_graph && (a->fwd_variant != h->variant || a->fwd_spin != h->spin_limit || h->inject)) {
+        cudaGraphExecDestroy(a->fwd_graph);
+        a->fwd_graph = nullptr;
+    }
+    if (a->use_graph && !a->fwd_graph && !h->inject &&
         cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         cudaGetLastError();
         a->use_graph = false;  // a stream that cannot be captured: launch eagerly
     }
-    if (a->use_graph && !a->fwd_graph) {  // capturing
+    if (a->use_graph && !a->fwd_graph && !h->inject) {  // capturing
+        a->fwd_variant = h->variant;
+        a->fwd_spin = h->spin_limit;
         const int cur = h->cur;
         const int64_t steps = h->steps, l0 = h->launches;
         const bool pending = h->pending_sample;

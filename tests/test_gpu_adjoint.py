@@ -207,3 +207,22 @@ def test_config_size_uy0_gradient_along_random_directions():
                 cd.append((ke[0] - ke[1]) / (2 * step))
             fd = (4.0 * cd[0] - cd[1]) / 3.0
             assert got == pytest.approx(fd, rel=1e-5), (k, got, fd, cd)
+
+
+def test_fp32_adjoint_graphs_follow_the_grid_tile_shape():
+    # the FP32 forward run and reverse sweep are replayed from CUDA graphs
+    # captured on first use; switching the grid's tile shape in between must
+    # not replay launches of the old shape (the two shapes compute the same
+    # bits, so the gradients are bitwise equal either way)
+    pb = inputs.khi(70, 45, 40, Dv=2.0, Drho=3.0, sample_every=5)
+    fields = [np.ascontiguousarray(a) for a in inputs.fields(pb)]
+    with klb.KlbAdjoint.from_problem(pb, "fp32", checkpoint_every=7) as adj:
+        res = []
+        for v in (adj.grid.variant, 1 - adj.grid.variant, 1 - adj.grid.variant):
+            adj.grid.variant = v
+            ke, gamma = adj.forward(*fields)
+            res.append((ke, gamma, adj.backward(1.0, 1.0)))
+    for ke, gamma, g in res[1:]:
+        assert ke == res[0][0] and gamma == res[0][1]
+        for a, b in zip(g, res[0][2]):
+            assert np.array_equal(a, b)
