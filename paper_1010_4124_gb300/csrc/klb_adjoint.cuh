@@ -5,17 +5,21 @@
 //   lambda^n = (dS/df^n)^T lambda^{n+1}
 // on the interior nodes, with every dependence through ghost nodes folded back
 // onto the interior node the ghost copies (periodic wrap, outflow copy).
-// Three parts:
-//   * faces: for each WENO5 face h (Eqs. 48-55 applied to F = v f), the
-//     sensitivity mu = dL/dh = (dt/dx)(lambda(right node) - lambda(left node))
-//     times the gradient of h with respect to its five stencil values,
-//     nonlinear weights included, written to a face-gradient buffer;
-//   * gather: each node collects, without atomics, the entries of the faces
-//     whose stencils contain it or one of its ghost images, and adds the
-//     adjoint of the BGK term: (1 - dt/tau) lambda + (dt/tau) (d f^(0)/df)^T lambda,
-//     the latter through the four moments (rho, rho u, E) that f^(0) depends on;
-//   * sources and the initial state: dK/df for K = sum rho u_y^2 / 2, and
-//     (d f^(0) / d(rho, u_x, u_y, T))^T lambda^0 for the initial fields.
+// A reverse step is three launches:
+//   * fold: the ghost-image sums the previous reverse step left in lambda's
+//     ghost cells are added to the nodes they image;
+//   * node: per node, the adjoint of the BGK term's f^(0) part,
+//     (dt/tau) (d f^(0)/df)^T lambda, carried through the four moments
+//     (rho, rho u, E) that f^(0) depends on;
+//   * tile: per tile and velocity, every WENO5 face h (Eqs. 48-55 applied to
+//     F = v f) whose stencil reaches the tile, its sensitivity
+//     mu = dL/dh = (dt/dx)(lambda(right node) - lambda(left node)) times the
+//     gradient of h with respect to its five stencil values, nonlinear weights
+//     included, kept in shared memory; each node then gathers the entries of
+//     the faces whose stencils contain it, plus (1 - dt/tau) lambda and the
+//     node term; ghost positions keep their sums for the next fold.
+// Sources and the initial state: dK/df for K = sum rho u_y^2 / 2, and
+// (d f^(0) / d(rho, u_x, u_y, T))^T lambda^0 for the initial fields.
 #pragma once
 #include "klb_device.cuh"
 #include "klb_launch.h"
@@ -154,53 +158,7 @@ __device__ __forceinline__ void feq_vjp_moments(const StepConst<T>& c, const Mom
 namespace fdlb {
 
 // ---------------------------------------------------------------------------
-// kernels (one thread per face row position or per node)
-// ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ T lam_at(const T* lam, const Geom& g, int q, int i, int j) {
-    if (i < 0 || i >= g.nx || j < 0 || j >= g.ny) return T(0);  // ghosts are not state variables
-    return lam[q * g.plane + (long long)(j + GY) * g.px + (i + GX)];
-}
-
-// the velocity of y slot k (the 12 velocities with v_y != 0: directions 1, 2,
-// 4 and 5 of each ring) and the y slot of velocity q
-__device__ __forceinline__ int yvel_of(int k) {
-    const int d = k % 4;
-    return 1 + 6 * (k / 4) + (d < 2 ? d : d + 1);
-}
-__device__ __forceinline__ int yslot_of(int q) {
-    const int d = dir_of(q);
-    return 4 * (ring_of(q) - 1) + (d < 3 ? d - 1 : d - 2);
-}
-
-// stencil positions that hold node i's value: the node itself and, next to a
-// periodic or outflow side, its ghost images (a fixed-equilibrium ghost is a
-// constant and carries no sensitivity)
-__device__ __forceinline__ int images(int i, int n, int per, int lo_out, int hi_out, int pos[8]) {
-    int m = 0;
-    if (per) {
-        for (int k = -3; k <= 3; ++k) {
-            const int p = i + k * n;
-            if (p >= -3 && p < n + 3) pos[m++] = p;
-        }
-        return m;
-    }
-    pos[m++] = i;
-    if (i == 0 && lo_out) {
-        pos[m++] = -1;
-        pos[m++] = -2;
-        pos[m++] = -3;
-    }
-    if (i == n - 1 && hi_out) {
-        pos[m++] = n;
-        pos[m++] = n + 1;
-        pos[m++] = n + 2;
-    }
-    return m;
-}
-
-// ---------------------------------------------------------------------------
-// The reverse step in two launches.
+// The reverse step in three launches.
 //
 // lambda^n_q(p) = (1 - dt/tau) lambda^{n+1}_q(p)
 //               + dt/tau sum_r lambda^{n+1}_r(p) d f^(0)_r(p) / d f_q(p)      (BGK, Eq. 28)
