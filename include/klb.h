@@ -134,8 +134,12 @@ int klb_get_f(klb_t* h, double* f, int on_device);
 
 /* Enqueue n time steps (Eq. 47) on the handle's stream and return without
  * waiting.  Each step is one launch of the fused step kernel (ghost images of
- * the new state are written by the same launch).  n >= 0.  Errors:
- * KLB_E_STATE (no klb_init_fields yet), KLB_E_INVAL, KLB_E_CUDA. */
+ * the new state are written by the same launch).  FP32 WENO5 handles replay
+ * runs of steps (at least 64, whole sampling periods, starting at a sampling
+ * point) from CUDA graphs captured on first use, one per buffer parity and
+ * sampling state; the results are bitwise those of one launch per step.
+ * n >= 0.  Errors: KLB_E_STATE (no klb_init_fields yet), KLB_E_INVAL,
+ * KLB_E_CUDA. */
 int klb_step(klb_t* h, int64_t n);
 
 /* Wait for the handle's stream; report device-side errors recorded since the
@@ -332,7 +336,10 @@ const char* klb_batch_last_error(const klb_batch_t* b);
  * (WENO5 including its nonlinear weights, f^(0) through the moments, BGK),
  * segment by segment from checkpoints taken every checkpoint_every steps
  * (the segment's states are recomputed), and ends with the sensitivities of
- * the initial fields (f^0 = f^(0)(rho, u, T)).
+ * the initial fields (f^0 = f^(0)(rho, u, T)).  In FP32 the forward run and
+ * the reverse sweep are captured into CUDA graphs on their first call and
+ * replayed (the objective's weights are data, not launch parameters); a
+ * change of the grid's tile shape or wait budget recaptures them.
  * ------------------------------------------------------------------------- */
 typedef struct klb_adj klb_adj_t;
 
@@ -367,7 +374,8 @@ int klb_adjoint_vjp(klb_adj_t* a, const double* lam_N, double* lam_0, int on_dev
 /* K_s of the last forward run (up to cap values into out; count in *count). */
 int klb_adjoint_samples(klb_adj_t* a, double* out, int64_t cap, int64_t* count);
 
-/* The forward grid (borrowed; for klb_get_f / klb_moments after a forward). */
+/* The forward grid (borrowed; for klb_get_f / klb_moments after a forward,
+ * or klb_set_variant to choose its FP32 tile shape). */
 klb_t* klb_adjoint_grid(klb_adj_t* a);
 const char* klb_adjoint_last_error(const klb_adj_t* a);
 
