@@ -150,6 +150,9 @@ def workload_problem(name: str, steps: int):
         pb = inputs.khi(2048, 2048, steps, Dv=16.0, Drho=16.0, modes=4, phase_seed=inputs.ROOFLINE_PHASE_SEED)
     elif name == "khi512":
         pb = inputs.khi(512, 512, steps)
+    elif name in ("khi8192", "khi16384"):  # the same profile on larger grids (2 x 5.1 / 20.4 GB of f)
+        n = int(name[3:])
+        pb = inputs.khi(n, n, steps, Dv=16.0, Drho=16.0, modes=4, phase_seed=inputs.ROOFLINE_PHASE_SEED)
     else:
         raise SystemExit(f"unknown workload {name}")
     pb.sample_every = 0
@@ -662,7 +665,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="khi4096", choices=["khi4096", "khi2048", "khi512"])
+    ap.add_argument("--workload", default="khi4096", choices=["khi4096", "khi2048", "khi512", "khi8192", "khi16384"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--variant", type=int, default=-1,
                     help="FP32 kernel tile shape (0: 32x16, 1: 32x8); -1 picks the faster by timing both")
