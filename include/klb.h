@@ -201,12 +201,9 @@ int64_t klb_launch_count(const klb_t* h);
 
 /* Kernel variant (tile shape) of the FP32 step: 0 = tiles of 32 x 16 nodes,
  * one CTA of 16 warps per SM; 1 = tiles of 32 x 8 nodes, two CTAs of 8 warps
- * per SM; 2 = tiles of 32 x 16 nodes, two CTAs of 8 warps per SM, each thread
- * two nodes in packed arithmetic (WENO5 grids outside batches; its
- * diagnostics are reduced by variant 0's kernel).  Every node is computed by
- * the same arithmetic in all, so the states are bitwise identical; only the
- * speed differs (the diagnostics sums may differ in the last bits, being
- * reduced in another order).  A new FP32
+ * per SM.  Every node is computed by the same arithmetic in both, so the
+ * states are bitwise identical; only the speed differs (the diagnostics sums
+ * may differ in the last bits, being reduced in another order).  A new FP32
  * handle starts with the shape measured faster for its size: 1 up to 40
  * sixteen-row tiles per SM (about 2048 x 1024 nodes on 152 SMs), 0 beyond.
  * The FP64 step has variant 0 only.  Synchronises the handle's stream.

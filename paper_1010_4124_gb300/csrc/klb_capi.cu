@@ -486,7 +486,7 @@ int klb_get_f(klb_t* h, double* f, int on_device) {
 // partial diagnostics records written by one launch of the current kernel
 static int records(const klb_t* h) {
     if (h->p.precision == KLB_FP64) return h->nparts;
-    return f32_grid(h->g.nx, h->g.ny, h->variant == 2 ? 0 : h->variant);  // variant 2: the 32 x 16 reduction
+    return f32_grid(h->g.nx, h->g.ny, h->variant);
 }
 
 int fdlb::handle_upload_descs(klb_t* h) {
@@ -522,18 +522,6 @@ static int one_step(klb_t* h) {
     if (h->pending_sample) parts = h->diag_partials;
     cudaError_t e;
     const int src = h->cur, dst = 1 - h->cur;
-    if (parts && h->p.precision == KLB_FP32 && h->variant == 2) {
-        // the two-rows-per-thread kernel fuses no diagnostics: the input
-        // state's sample is reduced by the stand-alone kernel first
-        e = launch_diag_f32(h->cf, h->g, (const float*)h->buf[src], parts, 2, h->stream);
-        if (e != cudaSuccess) return cuda_fail(h, e, "diagnostics kernel");
-        h->launches += 1;
-        e = launch_diag_finalize(parts, records(h), h->diag_ring, h->cap, h->nsamp_dev, h->err_dev, h->stream);
-        if (e != cudaSuccess) return cuda_fail(h, e, "diagnostics finalize");
-        h->launches += 1;
-        h->pending_sample = false;
-        parts = nullptr;
-    }
     if (h->p.precision == KLB_FP64)
         e = launch_step<double>(h->map[src], h->cd, h->g, (double*)h->buf[dst], parts, h->err_dev, h->spin_limit,
                                 h->inject, h->stream);
@@ -758,13 +746,11 @@ int klb_debug_bounds_probe(klb_t* h) {
 
 int klb_set_variant(klb_t* h, int variant) {
     if (!h) return KLB_E_INVAL;
-    if (variant < 0 || variant > 2) return fail(h, KLB_E_INVAL, "unknown kernel variant");
+    if (variant < 0 || variant > 1) return fail(h, KLB_E_INVAL, "unknown kernel variant");
     if (h->p.precision == KLB_FP64) {
         if (variant != 0) return fail(h, KLB_E_INVAL, "the FP64 step has one variant");
         return KLB_OK;
     }
-    if (variant == 2 && h->p.scheme != KLB_WENO5)
-        return fail(h, KLB_E_INVAL, "the two-rows-per-thread variant steps WENO5 grids only");
     CK(h, cudaStreamSynchronize(h->stream));
     const int old = h->variant;
     // put the old tile shape back (maps and descriptors); a rollback that

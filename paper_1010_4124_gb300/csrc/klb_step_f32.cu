@@ -2,7 +2,6 @@
 // launch) and its WENO5 instances; the lower-order schemes are instanced in
 // klb_step_f32_lo.cu.  The kernel itself is in klb_step_f32.cuh.
 #include "klb_step_f32.cuh"
-#include "klb_step_pair.cuh"
 
 namespace fdlb {
 
@@ -17,11 +16,9 @@ static int num_sms() {
     return n;
 }
 
-// tile heights offered: 16 rows (variant 0: one CTA of 16 warps per SM;
-// variant 2: two CTAs of 8 warps per SM, two rows per thread) or 8 rows
-// (variant 1: two CTAs of 8 warps per SM, whose phases interleave)
+// tile heights offered: 16 rows (one CTA of 16 warps per SM) or 8 rows (two
+// CTAs of 8 warps per SM, whose phases interleave)
 static int rows_of(int variant) { return variant == 1 ? 8 : 16; }
-static int ctas_per_sm(int variant) { return variant == 0 ? 1 : 2; }
 
 void f32_tiles(int nx, int ny, int variant, int* tiles_x, int* ntiles) {
     const int ty = rows_of(variant);
@@ -31,7 +28,7 @@ void f32_tiles(int nx, int ny, int variant, int* tiles_x, int* ntiles) {
 int f32_grid(int nx, int ny, int variant) {
     int tx, nt;
     f32_tiles(nx, ny, variant, &tx, &nt);
-    const int n = num_sms() * ctas_per_sm(variant);
+    const int n = num_sms() * (16 / rows_of(variant));
     return nt < n ? nt : n;
 }
 // The faster tile shape by grid size, measured on GB300 (4096^2: 16-row tiles
@@ -48,21 +45,9 @@ void f32_box(int variant, unsigned* bx, unsigned* by, unsigned* bz) {
     *bz = NQ;
 }
 
-static cudaError_t set_attr_pair() {
-    static bool done = false;
-    if (!done) {
-        cudaError_t e = cudaFuncSetAttribute(step_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)v4::SMEM_BYTES);
-        if (e != cudaSuccess) return e;
-        done = true;
-    }
-    return cudaSuccess;
-}
-
 cudaError_t prepare_f32_kernels() {
     num_sms();
-    cudaError_t e = set_attr_pair();
-    if (e == cudaSuccess) e = set_attr_f32<8, 0, false>();
+    cudaError_t e = set_attr_f32<8, 0, false>();
     if (e == cudaSuccess) e = set_attr_f32<16, 0, false>();
     if (e == cudaSuccess) e = set_attr_f32<8, 0, true>();
     return e != cudaSuccess ? e : set_attr_f32<16, 0, true>();
@@ -72,18 +57,9 @@ cudaError_t launch_step_f32(const StepConst<float>& c, const InstDesc* descs, in
                             double* diag_partials, int* err, long long spin_limit, int inject, int variant,
                             cudaStream_t stream) {
     if (ninst < 1 || ninst > kMaxInstances) return cudaErrorInvalidValue;
-    const int per_sm = ctas_per_sm(variant);
+    const int per_sm = 16 / rows_of(variant);
     const int grid = ntiles < num_sms() * per_sm ? ntiles : num_sms() * per_sm;
     if (grid < 1) return cudaSuccess;
-    if (variant == 2) {  // two rows per thread: one WENO5 grid, diagnostics reduced apart
-        if (ninst != 1 || diag_partials != nullptr || c.scheme != 0) return cudaErrorInvalidValue;
-        cudaError_t e = set_attr_pair();
-        if (e != cudaSuccess) return e;
-        PairConst pc;
-        make_pair_const(c, pc);
-        step_pair_kernel<<<grid, v4::NT, v4::SMEM_BYTES, stream>>>(c, pc, descs, ntiles, err, spin_limit, inject);
-        return cudaGetLastError();
-    }
     if (c.scheme != 0)
         return launch_step_f32_lo(c, descs, ninst, ntiles, diag_partials, err, spin_limit, inject,
                                   rows_of(variant), grid, stream);
@@ -111,7 +87,6 @@ cudaError_t launch_diag_f32_batch(const StepConst<float>& c, const DiagJob* jobs
 
 cudaError_t launch_diag_f32(const StepConst<float>& c, const Geom& g, const float* f, double* partials, int variant,
                             cudaStream_t s) {
-    if (variant == 2) variant = 0;  // the diagnostics of the 32 x 16 tiles
     int tiles_x, ntiles;
     f32_tiles(g.nx, g.ny, variant, &tiles_x, &ntiles);
     const int grid = f32_grid(g.nx, g.ny, variant);

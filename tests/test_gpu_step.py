@@ -140,7 +140,7 @@ def test_diagnostics_series_parity(prec, tol):
         assert np.abs(d[:, k] - dref[:, k]).max() <= bound * scale, (k, bound)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1])
 def test_fp32_diagnostics_equal_the_oracle_sums_of_the_same_state(variant):
     # The FP32 diagnostics (FP32 node values, compensated FP32 partial sums,
     # FP64 across warps and CTAs) against the oracle's FP64 diagnostics of the
@@ -466,14 +466,14 @@ def test_fp32_variants_are_bitwise_identical(bcx, bcy):
     pb = inputs.khi(300, 170, 30).with_(bc_x=(bcx, bcx), bc_y=(bcy, bcy))
     fields = inputs.fields(pb)
     out = []
-    for v in (0, 1, 2):
+    for v in (0, 1):
         with gpu_handle(pb, "fp32") as h:
             h.variant = v
             assert h.variant == v
             h.init_fields(*fields)
             h.step(30)
             out.append(h.get_f())
-    assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
+    assert np.array_equal(out[0], out[1])
 
 
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
@@ -510,14 +510,14 @@ def test_fp32_one_step_parity_every_size(nx, ny, bcx, bcy):
     f0 = perturbed_state(pb, fields, seed=5)
     ref = core.step(p, f0, fixed=core.fixed_ghosts(p, *fields))
     got = []
-    for v in (0, 1, 2):
+    for v in (0, 1):
         with gpu_handle(pb, "fp32") as h:
             h.variant = v
             h.init_fields(*[np.ascontiguousarray(a) for a in fields])
             h.set_f(np.ascontiguousarray(f0))
             h.step(1)
             got.append(h.get_f())
-    assert np.array_equal(got[0], got[1]) and np.array_equal(got[0], got[2])
+    assert np.array_equal(got[0], got[1])
     assert rel_err_global(got[0], ref) <= 2e-6
 
 
