@@ -84,7 +84,8 @@ typedef struct {
     int32_t diag_capacity;    /* samples kept on the device (0 = 4096); older samples are dropped */
     double eps;               /* WENO epsilon of Eq. 52; 0 selects the paper's 1e-6.  FP32
                                * WENO5 needs 3/4 eps / max(v)^2 >= 2e-19 (the squared
-                               * smoothness indicators stay normal FP32 numbers) and keeps
+                               * reciprocals of the smoothness indicators stay normal
+                               * FP32 numbers) and keeps
                                * its weights exact while the smallest indicator of a face
                                * is below 9e18 (differences of f up to about 1e9) */
     void* stream;             /* cudaStream_t to enqueue on; NULL = a stream owned by the handle */

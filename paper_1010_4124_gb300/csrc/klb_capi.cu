@@ -223,9 +223,10 @@ int klb_create(const klb_params* pin, klb_t** out) {
     if (p.scheme < KLB_WENO5 || p.scheme > KLB_TVD2) return fail(nullptr, KLB_E_INVAL, "unknown convection scheme");
 
     const double vmax = std::max(p.v[0], std::max(p.v[1], p.v[2]));
-    // FP32 WENO5 squares its smoothness indicators, each at least 3/4 eps / v_a^2
-    // for the velocity component v_a of its plane (the largest |v_a| is vmax):
-    // their squares and the weights' sum must stay normal FP32 numbers
+    // FP32 WENO5 squares the reciprocals of its smoothness indicators, each at
+    // least 3/4 eps / v_a^2 for the velocity component v_a of its plane (the
+    // largest |v_a| is vmax): those squares and the weights' sum must stay
+    // normal FP32 numbers
     if (p.precision == KLB_FP32 && p.scheme == KLB_WENO5 && p.eps > 0 && 0.75 * p.eps / (vmax * vmax) < 2e-19)
         return fail(nullptr, KLB_E_INVAL, "eps too small for the FP32 WENO5 weights (3/4 eps / max(v)^2 < 2e-19)");
     const double cfl = vmax * p.dt / std::min(p.dx, p.dy);

@@ -224,12 +224,13 @@ struct ArithF32 {
         // 1/6 folded in, and numerator and denominator both scaled by 10,
         //   h = c + (G1 w1 + G2 w2 + G3 w3) / (w1 + 6 w2 + 3 w3),
         //   G1 = 5/6 D2 + 1/3 D1, G2 = D2 + 2 D3, G3 = 2 D3 + e4 / 2,
-        // with w_q = 1 / s_q^2 (one reciprocal each, and one of the sum).
-        // Range: s_q^2 stays a normal FP32 number for 1.1e-19 <= s_q <= 1.8e19;
-        // s_q >= eps always, so eps (3/4 eps / v^2 of the finest velocity
-        // component) must be at least 1.1e-19, and the weights stay exact
-        // while the smallest indicator of a face is below 9e18 (differences
-        // of f up to about 1e9).  (A common denominator of products of the
+        // with w_q = (1 / s_q)^2: the reciprocal of each indicator, squared
+        // (the reciprocal starts as soon as the indicator is formed), and one
+        // reciprocal of the sum.  Range: (1 / s_q)^2 stays a normal FP32 number
+        // for 5.4e-20 <= s_q <= 9.2e18; s_q >= eps always, so eps (3/4 eps /
+        // v^2 of the finest velocity component) must be at least that, and the
+        // weights stay exact while the smallest indicator of a face is below
+        // 9e18 (differences of f up to about 1e9).  (A common denominator of products of the
         // squared indicators, one reciprocal per face, spans s^4: it fails
         // below eps ~ 2e-10 and above differences ~ 3e4.)
         // Every operation is an explicitly rounded multiply, add or fused
@@ -240,8 +241,8 @@ struct ArithF32 {
         const T s1 = fmaf(d1, fmaf(2.75f, d2, d1), fmaf(2.5f, a2, eps));
         const T s2 = fmaf(d2, fmaf(-1.25f, d3, d2), fmaf(d3, d3, eps));
         const T s3 = fmaf(e4, fmaf(2.75f, d3, e4), fmaf(2.5f, a3, eps));
-        const T w1 = rcp_approx(__fmul_rn(s1, s1)), w2 = rcp_approx(__fmul_rn(s2, s2));
-        const T w3 = rcp_approx(__fmul_rn(s3, s3));
+        const T r1 = rcp_approx(s1), r2 = rcp_approx(s2), r3 = rcp_approx(s3);
+        const T w1 = __fmul_rn(r1, r1), w2 = __fmul_rn(r2, r2), w3 = __fmul_rn(r3, r3);
         const T G1 = fmaf(5.f / 6.f, d2, __fmul_rn(1.f / 3.f, d1));
         const T t3 = __fadd_rn(d3, d3);  // 2 D3, shared by G2 and G3
         const T G2 = __fadd_rn(d2, t3);
@@ -263,10 +264,10 @@ struct ArithF32 {
         const float2 s1 = __ffma2_rn(d1, __ffma2_rn(k275, d2, d1), __ffma2_rn(k25, a2, eps));
         const float2 s2 = __ffma2_rn(d2, __ffma2_rn(kWenoPairs[3], d3, d2), __ffma2_rn(d3, d3, eps));
         const float2 s3 = __ffma2_rn(e4, __ffma2_rn(k275, d3, e4), __ffma2_rn(k25, a3, eps));
-        const float2 p1 = __fmul2_rn(s1, s1), p2 = __fmul2_rn(s2, s2), p3 = __fmul2_rn(s3, s3);
-        const float2 w1 = make_float2(rcp_approx(p1.x), rcp_approx(p1.y));
-        const float2 w2 = make_float2(rcp_approx(p2.x), rcp_approx(p2.y));
-        const float2 w3 = make_float2(rcp_approx(p3.x), rcp_approx(p3.y));
+        const float2 r1 = make_float2(rcp_approx(s1.x), rcp_approx(s1.y));
+        const float2 r2 = make_float2(rcp_approx(s2.x), rcp_approx(s2.y));
+        const float2 r3 = make_float2(rcp_approx(s3.x), rcp_approx(s3.y));
+        const float2 w1 = __fmul2_rn(r1, r1), w2 = __fmul2_rn(r2, r2), w3 = __fmul2_rn(r3, r3);
         const float2 G1 = __ffma2_rn(kWenoPairs[4], d2, __fmul2_rn(kWenoPairs[5], d1));
         const float2 t3 = __fadd2_rn(d3, d3);
         const float2 G2 = __fadd2_rn(d2, t3);

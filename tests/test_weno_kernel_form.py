@@ -89,7 +89,8 @@ def kernel_form_f32(a, b, c, d, e, eps34):
     """ArithF32::weno, operation by operation, in float32."""
     with np.errstate(all="ignore"):
         c, (s1, s2, s3), (G1, G2, G3) = _indicators_f32(a, b, c, d, e, eps34)
-        w1, w2, w3 = _rcp(_mul(s1, s1)), _rcp(_mul(s2, s2)), _rcp(_mul(s3, s3))
+        r1, r2, r3 = _rcp(s1), _rcp(s2), _rcp(s3)
+        w1, w2, w3 = _mul(r1, r1), _mul(r2, r2), _mul(r3, r3)
         num = _fma(G1, w1, _fma(G2, w2, _mul(G3, w3)))
         den = _fma(6.0, w2, _fma(3.0, w3, w1))
         return _fma(num, _rcp(den), c)
