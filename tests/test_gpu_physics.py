@@ -131,3 +131,37 @@ def test_paper_state_fields_after_1000_steps(state, Dv, Drho):
     errs = rel_err_fields(got, ref, p)
     print(f"state {state} after 1000 steps: {rel_err_global(got, ref):.2e} of the scale of f, {errs}")
     assert rel_err_global(got, ref) <= 1e-4 and max(errs["rho"], errs["u"], errs["T"]) <= 1e-4, errs
+
+
+def test_sod_shock_widths_at_the_papers_resolution():
+    # Sec. III.B's Sod runs: dx = 1e-3, dt = tau = 1e-5, to t = 0.2 (20000
+    # steps; the domain [0, 1] here, the paper does not state it).  The paper
+    # reports the WENO5 shock spread over about three to four cells and wider
+    # shocks for the lower-order schemes of Fig. 2 (FP64 runs of the CUDA
+    # path; the shock against the exact gamma = 2 solution, R8)
+    from oracle import riemann
+    left, right = (1.0, 0.0, 1.0), (0.125, 0.0, 0.1)
+    pb = inputs.sod(1000, 4, 20000, dt=1e-5, tau=1e-5)
+    t = pb.steps * pb.dt
+    x = (np.arange(pb.nx) + 0.5) * pb.dx
+    p_s = riemann.star_state(left, right, gamma=2.0)[0]
+    S = riemann.wave_speeds(left, right, gamma=2.0)[3]
+    lo, hi = 0.1 + 0.1 * (p_s - 0.1), 0.1 + 0.9 * (p_s - 0.1)
+    sel = (x > 0.5 + S * t - 0.1) & (x < 0.5 + S * t + 0.1)
+    width = {}
+    for scheme in ("weno5", "tvd", "upwind1"):
+        with klb.Klb.from_problem(pb, precision="fp64", scheme=scheme) as h:
+            h.init_fields(*inputs.fields(pb))
+            h.step(pb.steps)
+            r, ux, uy, T = h.moments()
+        pr = (r * T)[0]
+        xx, pp = x[sel], pr[sel]
+        width[scheme] = (np.interp(lo, pp[::-1], xx[::-1]) - np.interp(hi, pp[::-1], xx[::-1])) / pb.dx
+        if scheme == "weno5":
+            # the shock sits where the exact solution puts it
+            i = np.where((pp[:-1] >= 0.5 * (p_s + 0.1)) & (pp[1:] < 0.5 * (p_s + 0.1)))[0][-1]
+            xs = xx[i] + pb.dx * (pp[i] - 0.5 * (p_s + 0.1)) / (pp[i] - pp[i + 1])
+            assert abs(xs - (0.5 + S * t)) < 1.0 * pb.dx, (xs, 0.5 + S * t)
+    print("shock widths (cells) at dx = 1e-3, t = 0.2:", width)
+    assert 1.0 <= width["weno5"] <= 4.0, width
+    assert width["weno5"] < width["tvd"] < width["upwind1"], width
